@@ -1,0 +1,202 @@
+/*
+ * kd.h -- C ABI of the GB300 (sm_103a) FFT split-operator library for the 2D Dirac
+ * equation in a Gaussian-beam standing light wave.
+ *
+ * Paper: Ge, Ahrens & Shen, "Two-dimensional simulation of the spin-flip in the
+ * Kapitza-Dirac effect", arXiv 2307.01571.  Every call below names the passage that
+ * defines what it computes.
+ *
+ * Conventions shared by all calls
+ *  - All functions return KD_OK (0) or a negative KD_ERR_* code and never abort.
+ *    kd_last_error() returns a thread-local message describing the last failure.
+ *  - A spinor is an array of complex numbers laid out [ny][nx][4], point-major,
+ *    components in the Dirac (standard) representation (psi1..psi4), complex128
+ *    (interleaved doubles) for KD_FP64 simulations and complex64 for KD_FP32.
+ *    Row iy, column ix is the point (x_min + ix dx, y_min + iy dy) of the box at t = 0.
+ *  - `where` = KD_HOST for a host pointer (the call copies synchronously) or
+ *    KD_DEVICE for a device pointer on the simulation's GPU (the call is ordered on the
+ *    simulation's stream; the caller keeps the memory alive until the stream has
+ *    passed the call).
+ *  - The library owns its device buffers.  The caller owns every pointer it passes
+ *    and may free the parameter structs as soon as a call returns.
+ *  - Sizes: nx and ny are powers of two in [4, 4096].
+ *  - There is no CPU fallback: with no usable CUDA device kd_create fails with
+ *    KD_ERR_CUDA.
+ *  - A kd_sim is not thread-safe; use one per host thread or serialise calls.
+ */
+#ifndef KD_H
+#define KD_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KD_OK 0
+#define KD_ERR_ARG (-1)              /* invalid argument (null pointer, bad value) */
+#define KD_ERR_UNSUPPORTED_SIZE (-2) /* grid size not a power of two in [4, 4096] */
+#define KD_ERR_CUDA (-3)             /* a CUDA call failed, or no usable device */
+#define KD_ERR_NONFINITE (-4)        /* an observed norm was NaN or infinite */
+#define KD_ERR_NORM_DRIFT (-5)       /* observed norm left the watchdog tolerance */
+#define KD_ERR_TIMEOUT (-6)          /* a bounded device wait ran out */
+#define KD_ERR_STATE_MISMATCH (-7)   /* checkpoint does not match this simulation */
+#define KD_ERR_NOMEM (-8)            /* device allocation failed */
+
+#define KD_FP64 0 /* complex128 spinor, FP64 arithmetic throughout */
+#define KD_FP32 1 /* complex64 spinor, FP32 arithmetic; FP64-built phase tables */
+
+#define KD_HOST 0
+#define KD_DEVICE 1
+
+#define KD_FIELD_NONE 0     /* free particle */
+#define KD_FIELD_PLANE 1    /* plane-wave standing wave, A = -2 A0 sin(wt) cos(k x) e_y */
+#define KD_FIELD_GAUSS 2    /* Gaussian-beam standing wave, Sec. II.A */
+
+/* Unit system: electron mass, speed of light, reduced Planck constant, charge.
+ * Atomic units are {1, 137.035999, 1, -1}; natural units {1, 1, 1, -1}. */
+typedef struct { double m, c, hbar, q; } kd_units;
+
+/* Periodic box at t = 0 (Sec. II.D: 2048 x 128 points over 80 x 40 wavelengths). */
+typedef struct {
+    int32_t nx, ny;
+    double x_min, x_max, y_min, y_max;
+} kd_grid;
+
+/* Laser field, Eqs. (Equation_of_Gaussian_beam), (Phase_of_Gaussian_beam),
+ * (Equation_of_vector_potential), scalar potential zero.
+ *  a0        q A0 / (m c^2), dimensionless (the paper's A0 = 0.1 mc/q is a0 = 0.1)
+ *  k_L       wave number, omega = c k_L
+ *  epsilon   beam divergence, waist w0 = 1/(k_L epsilon), Rayleigh length k_L w0^2 / 2
+ *  env_T     length of a sin^2(pi t / env_T) envelope; 0 = continuous wave
+ *  phase0    added to omega t
+ *  p_shift_* constant-gauge offset: kinetic = canonical + p_shift (the paper's
+ *            A_m = 1.0 mc/q along y is p_shift_y = m c)
+ *  box_vy    speed of the co-moving box along y (rows sit at y + box_vy t); the frame
+ *            translation adds the phase exp(+i box_vy p_y dt / hbar) to each kinetic step */
+typedef struct {
+    int32_t kind;
+    int32_t longitudinal;
+    double a0, k_L, epsilon, env_T, phase0, p_shift_x, p_shift_y, box_vy;
+} kd_field;
+
+/* Gaussian wave packet, Eq. (Density_distribution_of_Gaussian_wave_packet):
+ * p0 kinetic centre momentum, r0 centre position (absolute, t = 0), sigma_p width,
+ * spin +1/-1 along x (basis 0, chi = (1, +-1)/sqrt 2) or along z (basis 1). */
+typedef struct {
+    double p0x, p0y, r0x, r0y, sigma_p;
+    int32_t spin, basis;
+} kd_packet;
+
+/* Momentum-space read-out windows (Sec. III.B, Tables I and II): the incoming and the
+ * diffracted peak, each the cells within half_width (infinity norm) of the grid point
+ * nearest to the given kinetic momentum, plus a single-cell read-out at target. */
+typedef struct {
+    double p_in_x, p_in_y, p_diff_x, p_diff_y, target_x, target_y;
+    double half_width;
+    int32_t basis; /* spin basis of c^+- : 0 = x-polarised (the paper's), 1 = z */
+    int32_t pad_;
+} kd_obs_spec;
+
+/* Observables of one position-space state (Sec. III).  Momentum-space values are
+ * discrete cell probabilities |DFT psi|^2 dx dy / P (they sum to the norm);
+ * c^+- = u^+-(pi)^dagger phi with normalised bispinors, Eq. (Equation_of_spin_projection). */
+typedef struct {
+    double t;
+    double norm;                       /* sum |psi|^2 dx dy, Eq. (probability_density) */
+    double pop_in, pop_diff;           /* window sums of |phi|^2 */
+    double cp_in, cm_in, cp_diff, cm_diff; /* window sums of |c+|^2, |c-|^2 */
+    double max_diff, cp_max_diff, cm_max_diff; /* maxima over the diffracted window */
+    double p_target, cp_target, cm_target;     /* values at the target cell */
+} kd_obs;
+
+typedef struct kd_sim kd_sim;
+
+/* Creates a simulation on the current CUDA device.  precision is KD_FP64 or KD_FP32.
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream) on which every
+ * device operation of this simulation is ordered.  The spinor starts at zero, t = 0.
+ * Errors: KD_ERR_ARG, KD_ERR_UNSUPPORTED_SIZE, KD_ERR_CUDA, KD_ERR_NOMEM. */
+int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
+              int32_t precision, void* cuda_stream, kd_sim** out);
+
+/* Sets psi to the packet: phi(p, 0) = u^s(p) rho(p) on the momentum grid
+ * (Sec. II.C), an inverse 2D FFT, and normalisation to sum |psi|^2 dx dy = 1.  Resets
+ * t to 0 and sets the default observation spec (windows around p0 and p0 + 2 hbar
+ * k_L e_x, half width hbar k_L / 2, target p0 + 2 hbar k_L e_x). */
+int kd_init_packet(kd_sim* sim, const kd_packet* packet);
+
+/* Replaces the observation spec used by kd_step and by kd_observe(sim, NULL, ...). */
+int kd_set_obs_spec(kd_sim* sim, const kd_obs_spec* spec);
+
+/* Copies a [ny][nx][4] spinor in (set) or out (get); layout in the header comment. */
+int kd_set_spinor(kd_sim* sim, const void* psi, int32_t where);
+int kd_get_spinor(kd_sim* sim, void* psi, int32_t where);
+
+/* Sets the time of the current state (and the step counter to 0), or reads them. */
+int kd_set_time(kd_sim* sim, double t);
+int kd_get_time(kd_sim* sim, double* t, int64_t* steps_done);
+
+/* Advances the state by nsteps Strang steps of length dt (Sec. II.D):
+ *   psi <- exp(-i dt V(t_{n+1})/2) F^-1 exp(-i dt K) F exp(-i dt V(t_n)/2) psi,
+ * with V = -q alpha.A (Eq. Hamiltonian operator, phi = 0), K = c alpha.pi + beta m c^2 -
+ * box_vy p_y evaluated per grid momentum in closed form, F the unnormalised 2D DFT.
+ * If obs_every > 0, the observables of the spec are recorded after every obs_every
+ * steps; up to obs_cap records go to obs_out (host memory) and *n_obs (may be NULL)
+ * receives how many were produced.  Returns KD_ERR_NONFINITE if a recorded norm was not
+ * finite and KD_ERR_NORM_DRIFT if one left the watchdog tolerance (the state is then
+ * the state after all nsteps).  On return the state is in position space at t + nsteps dt
+ * and, when obs_every > 0, the call has synchronised the stream. */
+int kd_step(kd_sim* sim, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs_out,
+            int64_t obs_cap, int64_t* n_obs);
+
+/* Observables of the current state with spec (NULL = the simulation's spec).  Synchronous. */
+int kd_observe(kd_sim* sim, const kd_obs_spec* spec, kd_obs* out);
+
+/* Per-cell momentum-space probabilities (Eqs. px_momentum_space_probability_density and
+ * Equation_of_spin_projection): out[ny][nx][3] doubles = (|phi|^2, |c+|^2, |c-|^2) in
+ * the given spin basis, cells in FFT order (index k -> k < n/2 ? k : k - n). */
+int kd_get_momentum_density(kd_sim* sim, int32_t basis, double* out, int32_t where);
+
+/* y-integrated density Phi(x) = sum_y |psi|^2 dy over the box, Eq.
+ * (y_integrated_probability_density): out[nx] doubles. */
+int kd_get_density_x(kd_sim* sim, double* out, int32_t where);
+
+/* Sets the watchdog of kd_step: a recorded norm that differs from the norm at the start
+ * of the call by more than tol times that norm makes kd_step return KD_ERR_NORM_DRIFT.
+ * tol <= 0 switches the drift check off (the default); the non-finite check is always
+ * on when observations are recorded. */
+int kd_set_watchdog(kd_sim* sim, double tol);
+
+/* Checkpoint: *size receives the byte count; with buf non-NULL and *size large enough
+ * the state (spinor, time, step counter and a hash of the parameters) is written to
+ * buf (host memory).  kd_set_state restores it; KD_ERR_STATE_MISMATCH if it was taken
+ * from a simulation with different parameters or precision. */
+int kd_get_state(kd_sim* sim, void* buf, size_t* size);
+int kd_set_state(kd_sim* sim, const void* buf, size_t size);
+
+/* Benchmark hook: enqueues `reps` back-to-back launches of one fused sweep on the
+ * simulation's stream, in place on the current state, and returns without waiting.
+ * kind 0 = x sweep (inverse x-FFT, full potential step exp(-i dt V(t)/hbar), forward
+ * x-FFT; the row pass of one Strang step, Sec. II.D), kind 1 = y sweep (forward y-FFT,
+ * kinetic step, inverse y-FFT; the column pass).  Uses the tables and time of the last
+ * kd_step call (KD_ERR_ARG before any kd_step).  The state is left in an unspecified
+ * mixed representation: call it on a scratch simulation, or restore a checkpoint after. */
+int kd_bench_sweep(kd_sim* sim, int32_t kind, int32_t reps);
+
+/* Number of kernel launches this simulation has enqueued so far (graph replays counted
+ * node by node). */
+int kd_get_launch_count(kd_sim* sim, int64_t* launches);
+
+/* Frees the simulation's device memory and CUDA graphs.  NULL is a no-op. */
+void kd_destroy(kd_sim* sim);
+
+/* Thread-local description of the last error ("" if none). */
+const char* kd_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int kd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -16,6 +16,6 @@ __all__ = ["workloads", "kd"]
 
 def __getattr__(name):
     if name == "kd":
-        from . import kd as _kd
-        return _kd
+        import importlib
+        return importlib.import_module(__name__ + ".kd")
     raise AttributeError(name)

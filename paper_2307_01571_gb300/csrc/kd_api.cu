@@ -1,0 +1,1176 @@
+// kd_api.cu -- host side of the C ABI declared in include/kd.h: validation, device
+// buffers, FP64 phase tables, the graph-captured step loop, observables and
+// checkpoints.  All arithmetic of the step runs in the sweep kernels (kd_sweep.cuh) and
+// in the small kernels below; nothing here computes on the host except FP64 tables of
+// at most max(nx, ny) entries.
+//
+// Paper: Ge, Ahrens & Shen, arXiv 2307.01571.  Sec. II.A (field), II.B (Hamiltonian,
+// bispinors, energy), II.C (packet, Fourier convention), II.D (split-operator step),
+// III (observables).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/kd.h"
+#include "kd_internal.h"
+
+using namespace kd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define KD_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? KD_ERR_NOMEM : KD_ERR_CUDA,    \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+bool pow2_in_range(int32_t n) { return n >= 4 && n <= 4096 && (n & (n - 1)) == 0; }
+int ilog2(int32_t n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+int32_t signed_index(int32_t k, int32_t n) { return k < n / 2 ? k : k - n; }
+
+struct ObsWin {  // window of signed momentum indices, integer, computed on the host
+    int ilo[2], ihi[2], jlo[2], jhi[2];
+    int it, jt;
+};
+
+struct GraphKey {
+    int chunk, last, obs;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(chunk, last, obs) < std::tie(o.chunk, o.last, o.obs);
+    }
+};
+
+}  // namespace
+
+struct kd_sim {
+    kd_units u;
+    kd_grid g;
+    kd_field f;
+    int prec;
+    size_t tsize;    // sizeof real
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    int device;
+    int lx, ly;
+    size_t P;
+    void* psi = nullptr;
+    void* work = nullptr;
+    void* tw_x = nullptr;
+    void* tw_y = nullptr;
+    void* xtab = nullptr;
+    void* kxtab = nullptr;
+    void* kytab = nullptr;
+    void* ktab = nullptr;
+    double ktab_dt = 0.0;
+    Clock* clock = nullptr;
+    StepScalars* steps = nullptr;
+    int64_t steps_cap = 0;
+    double* rowsum = nullptr;
+    double* md = nullptr;
+    double* scalar = nullptr;   // [0] norm of a reduction, [1] reference norm
+    kd_obs* obs_dev = nullptr;
+    int64_t obs_dev_cap = 0;
+    int* status = nullptr;
+    // host clock: t = t0 + step * dt_clock
+    double t0 = 0.0, dt_clock = 0.0;
+    int64_t step = 0;
+    kd_obs_spec spec{};
+    bool has_spec = false;
+    double watch_tol = 0.0;
+    // graphs of the step loop; cleared whenever a captured argument changes
+    std::map<GraphKey, std::pair<cudaGraphExec_t, int64_t>> graphs;  // exec, kernel nodes
+    int64_t launches = 0;
+    int64_t graph_obs_every = -1, graph_obs_cap = -1;
+    double graph_dt = 0.0, graph_t0 = 0.0;
+    ObsWin graph_win{};
+};
+
+namespace {
+
+size_t cbytes(const kd_sim* s) { return 2 * s->tsize; }                  // one complex
+size_t spinor_bytes(const kd_sim* s) { return s->P * 4 * cbytes(s); }
+
+double dxdy(const kd_sim* s) {
+    return (s->g.x_max - s->g.x_min) / s->g.nx * (s->g.y_max - s->g.y_min) / s->g.ny;
+}
+
+void clear_graphs(kd_sim* s) {
+    for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second.first);
+    s->graphs.clear();
+}
+
+// ---------------------------------------------------------------- small kernels ---
+
+// Kinetic table: C/P and c S/P with C = cos(E dt/hbar), S = sin(E dt/hbar)/E, E from
+// the relativistic energy-momentum relation (Sec. II.B), pi = canonical + p_shift.
+// FP64 throughout; rounded once to the sweep precision.
+template <typename T>
+__global__ void k_ktab(T* out, int nx, int ny, double dpx, double dpy, double shx, double shy,
+                       double c, double mc2, double hbar, double dt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx * ny) return;
+    const int kx = i % nx, ky = i / nx;
+    const double px = dpx * (kx < nx / 2 ? kx : kx - nx) + shx;
+    const double py = dpy * (ky < ny / 2 ? ky : ky - ny) + shy;
+    const double E = sqrt(mc2 * mc2 + c * c * (px * px + py * py));
+    double sn, cs;
+    sincos(E * dt / hbar, &sn, &cs);
+    const double invP = 1.0 / ((double)nx * (double)ny);
+    out[2 * i] = (T)(cs * invP);
+    out[2 * i + 1] = (T)(c * sn / E * invP);
+}
+
+// Time-dependent scalars of the standing wave for the steps of one kd_step call:
+// s(t) = a0 f(t) sin(omega t + phase0) and the co-moving box offset.
+__global__ void k_step_scalars(StepScalars* out, int64_t n, double t0, int64_t step0, double dt,
+                               double a0, double omega, double phase0, double env_T,
+                               double box_vy) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > n) return;
+    const double t = t0 + (double)(step0 + i) * dt;
+    double f = 1.0;
+    if (env_T > 0.0) {
+        if (t < 0.0 || t > env_T) f = 0.0;
+        else { const double sv = sin(kPi * t / env_T); f = sv * sv; }
+    }
+    StepScalars r;
+    r.t = t;
+    r.s = a0 * f * sin(omega * t + phase0);
+    r.Y = box_vy * t;
+    r.pad = 0.0;
+    out[i] = r;
+}
+
+__global__ void k_set_clock(Clock* c, long long step) { c->step = step; c->base = step; }
+__global__ void k_advance_clock(Clock* c, int n) { c->step += n; }
+
+// Per-row sum of |psi|^2 (fixed-order tree: bitwise reproducible).
+template <typename T>
+__global__ void k_rowsum(const T* psi, int nx, double* rowsum) {
+    __shared__ double red[256];
+    const int row = blockIdx.x;
+    const T* p = psi + (size_t)row * nx * 8;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nx * 8; i += blockDim.x) acc += (double)p[i] * (double)p[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) rowsum[row] = red[0];
+}
+
+// Phi(x) = sum_y |psi|^2 dy, one thread per column, rows in order.
+template <typename T>
+__global__ void k_density_x(const T* psi, int nx, int ny, double dy, double* out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    double acc = 0.0;
+    for (int y = 0; y < ny; ++y) {
+        const T* p = psi + ((size_t)y * nx + x) * 8;
+        double s = 0.0;
+        for (int i = 0; i < 8; ++i) s += (double)p[i] * (double)p[i];
+        acc += s;
+    }
+    out[x] = acc * dy;
+}
+
+// Sum of the row sums times dx dy into scalar[slot]; fixed order.
+__global__ void k_norm(const double* rowsum, int ny, double cell, double* scalar, int slot) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) acc += rowsum[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scalar[slot] = red[0] * cell;
+}
+
+template <typename T>
+__global__ void k_scale_by_norm(T* psi, size_t n, const double* scalar) {
+    const double nr = scalar[0];
+    const T s = (T)(nr > 0.0 ? 1.0 / sqrt(nr) : 0.0);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        psi[i] *= s;
+}
+
+// Normalised positive-energy bispinor u^s(pi) of Eq. (Spinors_of_Dirac_equation) with
+// unit chi (x-polarised chi = (1, +-1)/sqrt 2, or z-polarised); Dirac component order.
+__device__ void bispinor(double c, double mc2, double pix, double piy, int spin, int basis,
+                         double2 u[4]) {
+    const double E = sqrt(mc2 * mc2 + c * c * (pix * pix + piy * piy));
+    const double nrm = sqrt((E + mc2) / (2.0 * E));
+    double2 chi[2];
+    if (basis == 1) {
+        chi[0] = make_double2(spin > 0 ? 1.0 : 0.0, 0.0);
+        chi[1] = make_double2(spin > 0 ? 0.0 : 1.0, 0.0);
+    } else {
+        const double r = 0.70710678118654752440;
+        chi[0] = make_double2(r, 0.0);
+        chi[1] = make_double2(spin > 0 ? r : -r, 0.0);
+    }
+    // lower = c sigma.pi chi / (E + mc^2); sigma.pi = [[0, pix - i piy], [pix + i piy, 0]]
+    const double f = c / (E + mc2);
+    const double2 lo0 = make_double2(f * (pix * chi[1].x + piy * chi[1].y), f * (pix * chi[1].y - piy * chi[1].x));
+    const double2 lo1 = make_double2(f * (pix * chi[0].x - piy * chi[0].y), f * (pix * chi[0].y + piy * chi[0].x));
+    u[0] = make_double2(nrm * chi[0].x, nrm * chi[0].y);
+    u[1] = make_double2(nrm * chi[1].x, nrm * chi[1].y);
+    u[2] = make_double2(nrm * lo0.x, nrm * lo0.y);
+    u[3] = make_double2(nrm * lo1.x, nrm * lo1.y);
+}
+
+// phi(p, 0) = u^s(pi) rho(pi), rho = exp(-|pi - p0|^2/(4 sigma^2) - i (r0 - origin).p/hbar)
+// (Sec. II.C); written in the internal component order.
+template <typename T>
+__global__ void k_packet(T* psi, int nx, int ny, double dpx, double dpy, double shx, double shy,
+                         double p0x, double p0y, double rx, double ry, double sig, int spin,
+                         int basis, double c, double mc2, double hbar) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx * ny) return;
+    const int kx = i % nx, ky = i / nx;
+    const double px = dpx * (kx < nx / 2 ? kx : kx - nx), py = dpy * (ky < ny / 2 ? ky : ky - ny);
+    const double pix = px + shx, piy = py + shy;
+    const double ddx = pix - p0x, ddy = piy - p0y;
+    const double mag = exp(-(ddx * ddx + ddy * ddy) / (4.0 * sig * sig));
+    double sn, cs;
+    sincos(-(rx * px + ry * py) / hbar, &sn, &cs);
+    double2 u[4];
+    bispinor(c, mc2, pix, piy, spin, basis, u);
+    for (int s = 0; s < 4; ++s) {
+        const double2 uu = u[perm_to_dirac(s)];
+        psi[(size_t)i * 8 + 2 * s] = (T)(mag * (uu.x * cs - uu.y * sn));
+        psi[(size_t)i * 8 + 2 * s + 1] = (T)(mag * (uu.x * sn + uu.y * cs));
+    }
+}
+
+// Per-cell momentum-space probabilities from phi = DFT psi (internal order):
+// (|phi|^2, |c+|^2, |c-|^2) dx dy / P, c^s = u^s(pi)^dagger phi.
+template <typename T>
+__global__ void k_momentum_density(const T* phi, int nx, int ny, double dpx, double dpy,
+                                   double shx, double shy, double c, double mc2, int basis,
+                                   double cellw, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx * ny) return;
+    const int kx = i % nx, ky = i / nx;
+    const double pix = dpx * (kx < nx / 2 ? kx : kx - nx) + shx;
+    const double piy = dpy * (ky < ny / 2 ? ky : ky - ny) + shy;
+    double2 f[4];
+    for (int s = 0; s < 4; ++s)
+        f[perm_to_dirac(s)] = make_double2((double)phi[(size_t)i * 8 + 2 * s], (double)phi[(size_t)i * 8 + 2 * s + 1]);
+    double p2 = 0.0;
+    for (int d = 0; d < 4; ++d) p2 += f[d].x * f[d].x + f[d].y * f[d].y;
+    double cpm[2];
+    for (int si = 0; si < 2; ++si) {
+        double2 u[4];
+        bispinor(c, mc2, pix, piy, si == 0 ? 1 : -1, basis, u);
+        double re = 0.0, im = 0.0;
+        for (int d = 0; d < 4; ++d) {  // conj(u) * f
+            re += u[d].x * f[d].x + u[d].y * f[d].y;
+            im += u[d].x * f[d].y - u[d].y * f[d].x;
+        }
+        cpm[si] = re * re + im * im;
+    }
+    out[(size_t)i * 3 + 0] = p2 * cellw;
+    out[(size_t)i * 3 + 1] = cpm[0] * cellw;
+    out[(size_t)i * 3 + 2] = cpm[1] * cellw;
+}
+
+// One observation record from the row sums and the momentum density: window sums over
+// fixed index ranges in a fixed order (bitwise reproducible), status bits for the
+// watchdog (1: non-finite norm, 2: drift beyond tol relative to scalar[1]).
+__global__ void k_obs_reduce(const double* rowsum, const double* md, int nx, int ny, double cell,
+                             ObsWin w, const StepScalars* steps, const Clock* clock, int n_local,
+                             double t_fixed, int64_t obs_every, int64_t cap, kd_obs* out,
+                             const double* scalar, double tol, int* status) {
+    __shared__ double red[256];
+    const int tid = threadIdx.x;
+    auto tree = [&](double v) -> double {
+        red[tid] = v;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (tid < s) red[tid] += red[tid + s];
+            __syncthreads();
+        }
+        const double r = red[0];
+        __syncthreads();
+        return r;
+    };
+    auto treemax = [&](double v) -> double {
+        red[tid] = v;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
+            __syncthreads();
+        }
+        const double r = red[0];
+        __syncthreads();
+        return r;
+    };
+    double acc = 0.0;
+    for (int i = tid; i < ny; i += blockDim.x) acc += rowsum[i];
+    const double norm = tree(acc) * cell;
+    double sums[2][3], mx[3] = {0, 0, 0};
+    for (int wi = 0; wi < 2; ++wi) {
+        const int wx = w.ihi[wi] - w.ilo[wi] + 1, wy = w.jhi[wi] - w.jlo[wi] + 1;
+        double a[3] = {0, 0, 0}, m[3] = {0, 0, 0};
+        for (int q = tid; q < wx * wy; q += blockDim.x) {
+            const int i = w.ilo[wi] + q % wx, j = w.jlo[wi] + q / wx;
+            const int kx = (i + nx) % nx, ky = (j + ny) % ny;
+            const double* o = md + ((size_t)ky * nx + kx) * 3;
+            for (int k = 0; k < 3; ++k) { a[k] += o[k]; m[k] = fmax(m[k], o[k]); }
+        }
+        for (int k = 0; k < 3; ++k) sums[wi][k] = tree(a[k]);
+        if (wi == 1)
+            for (int k = 0; k < 3; ++k) mx[k] = treemax(m[k]);
+    }
+    if (tid == 0) {
+        int64_t slot = 0;
+        double t = t_fixed;
+        if (clock) {
+            const long long sidx = (clock->step - clock->base) + n_local;
+            slot = sidx / obs_every - 1;
+            t = steps[sidx].t;
+        }
+        const int kx = (w.it + nx) % nx, ky = (w.jt + ny) % ny;
+        const double* o = md + ((size_t)ky * nx + kx) * 3;
+        kd_obs r;
+        r.t = t;
+        r.norm = norm;
+        r.pop_in = sums[0][0]; r.cp_in = sums[0][1]; r.cm_in = sums[0][2];
+        r.pop_diff = sums[1][0]; r.cp_diff = sums[1][1]; r.cm_diff = sums[1][2];
+        r.max_diff = mx[0]; r.cp_max_diff = mx[1]; r.cm_max_diff = mx[2];
+        r.p_target = o[0]; r.cp_target = o[1]; r.cm_target = o[2];
+        if (slot >= 0 && slot < cap) out[slot] = r;
+        int st = 0;
+        if (!isfinite(norm)) st |= 1;
+        if (tol > 0.0 && fabs(norm - scalar[1]) > tol * scalar[1]) st |= 2;
+        if (st && status) atomicOr(status, st);
+    }
+}
+
+// Layout conversion between the ABI's Dirac order and the internal (psi1, psi4, psi2, psi3).
+template <typename T>
+__global__ void k_permute(const T* in, T* out, size_t npts, int to_internal) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npts;
+         i += (size_t)gridDim.x * blockDim.x) {
+        T v[8];
+        for (int k = 0; k < 8; ++k) v[k] = in[i * 8 + k];
+        for (int s = 0; s < 4; ++s) {
+            const int d = perm_to_dirac(s);
+            if (to_internal) { out[i * 8 + 2 * s] = v[2 * d]; out[i * 8 + 2 * s + 1] = v[2 * d + 1]; }
+            else { out[i * 8 + 2 * d] = v[2 * s]; out[i * 8 + 2 * d + 1] = v[2 * s + 1]; }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host helpers ----
+
+int grid_blocks(size_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+template <typename T> int upload_tables_t(kd_sim* s) {
+    const int nx = s->g.nx, ny = s->g.ny;
+    // twiddles exp(-2 pi i m / N), FP64 then rounded
+    for (int ax = 0; ax < 2; ++ax) {
+        const int n = ax == 0 ? nx : ny;
+        std::vector<T> tw(2 * n);
+        for (int m = 0; m < n; ++m) {
+            const double a = 2.0 * kPi * m / n;
+            tw[2 * m] = (T)cos(a);
+            tw[2 * m + 1] = (T)(-sin(a));
+        }
+        KD_CUDA(cudaMemcpy(ax == 0 ? s->tw_x : s->tw_y, tw.data(), tw.size() * sizeof(T),
+                           cudaMemcpyHostToDevice));
+    }
+    // per-x field table (Eqs. Equation_of_Gaussian_beam, Phase_of_Gaussian_beam and w(x)):
+    // theta0 = (-k x + atan(x/x_R)) mod 2 pi, zeta = atan(x/x_R), x/(x_R w^2), w0/w, 1/w^2,
+    // 1/w; for the plane wave slot 0 holds cos(k x).
+    std::vector<T> xt(6 * (size_t)nx, (T)0);
+    const double dx = (s->g.x_max - s->g.x_min) / nx;
+    const double k = s->f.k_L;
+    for (int i = 0; i < nx; ++i) {
+        const double x = s->g.x_min + i * dx;
+        if (s->f.kind == KD_FIELD_PLANE) {
+            xt[i] = (T)cos(k * x);
+        } else if (s->f.kind == KD_FIELD_GAUSS) {
+            const double w0 = 1.0 / (k * s->f.epsilon);
+            const double xR = k * w0 * w0 / 2.0;
+            const double w = w0 * sqrt(1.0 + x * x / (xR * xR));
+            const double zeta = atan(x / xR);
+            xt[i] = (T)remainder(-k * x + zeta, 2.0 * kPi);
+            xt[nx + i] = (T)zeta;
+            xt[2 * nx + i] = (T)(x / (xR * w * w));
+            xt[3 * nx + i] = (T)(w0 / w);
+            xt[4 * nx + i] = (T)(1.0 / (w * w));
+            xt[5 * nx + i] = (T)(1.0 / w);
+        }
+    }
+    KD_CUDA(cudaMemcpy(s->xtab, xt.data(), xt.size() * sizeof(T), cudaMemcpyHostToDevice));
+    // kinetic x momentum per column
+    std::vector<T> kx(nx);
+    const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
+    for (int i = 0; i < nx; ++i) kx[i] = (T)(dpx * signed_index(i, nx) + s->f.p_shift_x);
+    KD_CUDA(cudaMemcpy(s->kxtab, kx.data(), kx.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return KD_OK;
+}
+
+// Tables that depend on dt: the kinetic table (device, FP64) and the per-row
+// (pi_y, cos, sin of the frame phase box_vy p_y dt / hbar).
+template <typename T> int build_dt_tables_t(kd_sim* s, double dt) {
+    const int nx = s->g.nx, ny = s->g.ny;
+    const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
+    const double dpy = s->u.hbar * 2.0 * kPi / (s->g.y_max - s->g.y_min);
+    const double mc2 = s->u.m * s->u.c * s->u.c;
+    k_ktab<T><<<grid_blocks(s->P, 256), 256, 0, s->stream>>>(
+        (T*)s->ktab, nx, ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y, s->u.c, mc2, s->u.hbar, dt);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    std::vector<T> ky(4 * (size_t)ny);
+    for (int j = 0; j < ny; ++j) {
+        const double py = dpy * signed_index(j, ny);
+        const double ph = s->f.box_vy * py * dt / s->u.hbar;
+        ky[4 * j] = (T)(py + s->f.p_shift_y);
+        ky[4 * j + 1] = (T)cos(ph);
+        ky[4 * j + 2] = (T)sin(ph);
+        ky[4 * j + 3] = (T)0;
+    }
+    KD_CUDA(cudaMemcpyAsync(s->kytab, ky.data(), ky.size() * sizeof(T), cudaMemcpyHostToDevice,
+                            s->stream));
+    KD_CUDA(cudaStreamSynchronize(s->stream));
+    s->ktab_dt = dt;
+    return KD_OK;
+}
+
+int build_dt_tables(kd_sim* s, double dt) {
+    return s->prec == KD_FP64 ? build_dt_tables_t<double>(s, dt) : build_dt_tables_t<float>(s, dt);
+}
+
+cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* out, int n_local,
+                  double tau) {
+    SweepArgs a{};
+    a.in = in;
+    a.out = out;
+    a.nx = s->g.nx;
+    a.ny = s->g.ny;
+    a.op = op;
+    a.tw = axis == AXIS_X ? s->tw_x : s->tw_y;
+    a.clock = s->clock;
+    a.steps = s->steps;
+    a.n_local = n_local;
+    a.kind = s->f.kind;
+    a.longitudinal = s->f.longitudinal;
+    a.kappa = tau * s->u.m * s->u.c * s->u.c / s->u.hbar;
+    a.eps4 = 4.0 * s->f.epsilon;
+    a.y_min = s->g.y_min;
+    a.dy = (s->g.y_max - s->g.y_min) / s->g.ny;
+    a.xtab = s->xtab;
+    a.ktab = s->ktab;
+    a.kxtab = s->kxtab;
+    a.kytab = s->kytab;
+    a.mc = s->u.m * s->u.c;
+    const int logn = axis == AXIS_X ? s->lx : s->ly;
+    ++s->launches;
+    return s->prec == KD_FP64 ? launch_sweep_f64(axis, shape, logn, a, s->stream)
+                              : launch_sweep_f32(axis, shape, logn, a, s->stream);
+}
+
+#define KD_LAUNCH(expr)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(KD_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));          \
+    } while (0)
+
+int rowsum_launch(kd_sim* s, const void* psi) {
+    if (s->prec == KD_FP64) k_rowsum<double><<<s->g.ny, 256, 0, s->stream>>>((const double*)psi, s->g.nx, s->rowsum);
+    else k_rowsum<float><<<s->g.ny, 256, 0, s->stream>>>((const float*)psi, s->g.nx, s->rowsum);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    return KD_OK;
+}
+
+int ensure_md(kd_sim* s) {
+    if (!s->md) KD_CUDA(cudaMalloc(&s->md, s->P * 3 * sizeof(double)));
+    return KD_OK;
+}
+
+// psi (position space) -> work = DFT psi (internal order) -> md
+int momentum_density_launch(kd_sim* s, int basis, double* out) {
+    const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
+    const double dpy = s->u.hbar * 2.0 * kPi / (s->g.y_max - s->g.y_min);
+    const double mc2 = s->u.m * s->u.c * s->u.c;
+    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_NONE, s->psi, s->work, 0, 0.0));
+    KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F1, OP_NONE, s->work, s->work, 0, 0.0));
+    const double cellw = dxdy(s) / (double)s->P;
+    if (s->prec == KD_FP64)
+        k_momentum_density<double><<<grid_blocks(s->P, 256), 256, 0, s->stream>>>(
+            (const double*)s->work, s->g.nx, s->g.ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y,
+            s->u.c, mc2, basis, cellw, out);
+    else
+        k_momentum_density<float><<<grid_blocks(s->P, 256), 256, 0, s->stream>>>(
+            (const float*)s->work, s->g.nx, s->g.ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y,
+            s->u.c, mc2, basis, cellw, out);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    return KD_OK;
+}
+
+// Window of signed indices around the grid point nearest to a kinetic momentum:
+// centre round((pi - p_shift)/dp), half width floor(h/dp), clamped to the grid.
+int window_axis(double pic, double shift, double dp, double h, int n, int* lo, int* hi, int* c) {
+    const double v = floor((pic - shift) / dp + 0.5);
+    if (!(v >= -(double)(n / 2) && v <= (double)(n / 2 - 1))) return -1;
+    const int cc = (int)v;
+    const int w = (int)floor(h / dp + 1e-9);
+    if (w < 0) return -1;
+    *c = cc;
+    *lo = cc - w < -(n / 2) ? -(n / 2) : cc - w;
+    *hi = cc + w > n / 2 - 1 ? n / 2 - 1 : cc + w;
+    return 0;
+}
+
+int make_window(const kd_sim* s, const kd_obs_spec* sp, ObsWin* w) {
+    if (!(sp->half_width >= 0.0)) return fail(KD_ERR_ARG, "obs spec half_width must be >= 0");
+    if (sp->basis != 0 && sp->basis != 1) return fail(KD_ERR_ARG, "obs spec basis must be 0 or 1");
+    const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
+    const double dpy = s->u.hbar * 2.0 * kPi / (s->g.y_max - s->g.y_min);
+    const double cx[3] = {sp->p_in_x, sp->p_diff_x, sp->target_x};
+    const double cy[3] = {sp->p_in_y, sp->p_diff_y, sp->target_y};
+    for (int k = 0; k < 3; ++k) {
+        int lo, hi, c, lo2, hi2, c2;
+        if (window_axis(cx[k], s->f.p_shift_x, dpx, sp->half_width, s->g.nx, &lo, &hi, &c) ||
+            window_axis(cy[k], s->f.p_shift_y, dpy, sp->half_width, s->g.ny, &lo2, &hi2, &c2))
+            return fail(KD_ERR_ARG, "obs spec momentum %d lies outside the momentum grid", k);
+        if (k < 2) { w->ilo[k] = lo; w->ihi[k] = hi; w->jlo[k] = lo2; w->jhi[k] = hi2; }
+        else { w->it = c; w->jt = c2; }
+    }
+    return KD_OK;
+}
+
+// Observation of the position-space state psi: row sums, forward 2D FFT into work,
+// momentum density, window reduction into out[slot].
+int observe_launch(kd_sim* s, const ObsWin& w, int basis, bool in_step, int n_local, double t_fixed,
+                   int64_t obs_every, int64_t cap, kd_obs* out) {
+    int rc = ensure_md(s);
+    if (rc) return rc;
+    rc = rowsum_launch(s, s->psi);
+    if (rc) return rc;
+    rc = momentum_density_launch(s, basis, s->md);
+    if (rc) return rc;
+    k_obs_reduce<<<1, 256, 0, s->stream>>>(s->rowsum, s->md, s->g.nx, s->g.ny, dxdy(s), w, s->steps,
+                                           in_step ? s->clock : nullptr, n_local, t_fixed,
+                                           obs_every, cap, out, s->scalar, s->watch_tol, s->status);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    return KD_OK;
+}
+
+int ensure_steps(kd_sim* s, int64_t n) {
+    if (n + 1 <= s->steps_cap) return KD_OK;
+    clear_graphs(s);
+    if (s->steps) cudaFree(s->steps);
+    s->steps = nullptr;
+    int64_t cap = 1024;
+    while (cap < n + 1) cap *= 2;
+    KD_CUDA(cudaMalloc(&s->steps, cap * sizeof(StepScalars)));
+    s->steps_cap = cap;
+    return KD_OK;
+}
+
+int ensure_obs(kd_sim* s, int64_t n) {
+    if (n <= s->obs_dev_cap) return KD_OK;
+    clear_graphs(s);
+    if (s->obs_dev) cudaFree(s->obs_dev);
+    s->obs_dev = nullptr;
+    int64_t cap = 16;
+    while (cap < n) cap *= 2;
+    KD_CUDA(cudaMalloc(&s->obs_dev, cap * sizeof(kd_obs)));
+    s->obs_dev_cap = cap;
+    return KD_OK;
+}
+
+// Enqueues one chunk of `chunk` steps starting from the "open" state (x sweep of the
+// opening half already applied): chunk-1 merged steps, then the chunk's last step,
+// which closes (last chunk, or an observation point) or merges.
+int enqueue_chunk(kd_sim* s, double dt, int chunk, bool last, bool obs, const ObsWin& w,
+                  int64_t obs_every, int64_t cap) {
+    for (int i = 1; i <= chunk; ++i) {
+        KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F1F2, OP_KINETIC, s->psi, s->psi, 0, 0.0));
+        if (i < chunk) {
+            KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F1F2, OP_POTENTIAL, s->psi, s->psi, i, dt));
+        } else if (last || obs) {
+            KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F1, OP_POTENTIAL, s->psi, s->psi, i, 0.5 * dt));
+            if (obs) {
+                int rc = observe_launch(s, w, s->spec.basis, true, i, 0.0, obs_every, cap, s->obs_dev);
+                if (rc) return rc;
+            }
+            if (!last) KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_POTENTIAL, s->psi, s->psi, i, 0.5 * dt));
+        } else {
+            KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F1F2, OP_POTENTIAL, s->psi, s->psi, i, dt));
+        }
+    }
+    k_advance_clock<<<1, 1, 0, s->stream>>>(s->clock, chunk);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    return KD_OK;
+}
+
+int run_chunk(kd_sim* s, double dt, int chunk, bool last, bool obs, const ObsWin& w,
+              int64_t obs_every, int64_t cap) {
+    GraphKey key{chunk, last ? 1 : 0, obs ? 1 : 0};
+    auto it = s->graphs.find(key);
+    if (it == s->graphs.end()) {
+        // capture on the private stream, launch on the simulation's stream
+        cudaStream_t user = s->stream;
+        s->stream = s->cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            s->stream = user;
+            return fail(KD_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+        }
+        const int64_t before = s->launches;
+        int rc = enqueue_chunk(s, dt, chunk, last, obs, w, obs_every, cap);
+        const int64_t nodes = s->launches - before;
+        s->launches = before;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(s->stream, &graph);
+        s->stream = user;
+        if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) return fail(KD_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(KD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        it = s->graphs.emplace(key, std::make_pair(exec, nodes)).first;
+    }
+    KD_CUDA(cudaGraphLaunch(it->second.first, s->stream));
+    s->launches += it->second.second;
+    return KD_OK;
+}
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+uint64_t param_hash(const kd_sim* s) {
+    uint64_t h = 1469598103934665603ull;
+    h = fnv(h, &s->u, sizeof s->u);
+    h = fnv(h, &s->g, sizeof s->g);
+    h = fnv(h, &s->f, sizeof s->f);
+    h = fnv(h, &s->prec, sizeof s->prec);
+    return h;
+}
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t nx, ny, prec, pad;
+    uint64_t hash;
+    double t0, dt_clock;
+    int64_t step;
+    uint64_t payload;
+};
+
+int check_sim(kd_sim* s) {
+    if (!s) return fail(KD_ERR_ARG, "null simulation");
+    cudaError_t e = cudaSetDevice(s->device);
+    if (e != cudaSuccess) return fail(KD_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return KD_OK;
+}
+
+int copy_in(kd_sim* s, const void* psi, int32_t where) {
+    const size_t bytes = spinor_bytes(s);
+    const void* src = psi;
+    if (where == KD_HOST) {
+        KD_CUDA(cudaMemcpyAsync(s->work, psi, bytes, cudaMemcpyHostToDevice, s->stream));
+        src = s->work;
+    }
+    const int blocks = grid_blocks(s->P, 256) < 4096 ? grid_blocks(s->P, 256) : 4096;
+    if (s->prec == KD_FP64) k_permute<double><<<blocks, 256, 0, s->stream>>>((const double*)src, (double*)s->psi, s->P, 1);
+    else k_permute<float><<<blocks, 256, 0, s->stream>>>((const float*)src, (float*)s->psi, s->P, 1);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    if (where == KD_HOST) KD_CUDA(cudaStreamSynchronize(s->stream));
+    return KD_OK;
+}
+
+int copy_out(kd_sim* s, void* psi, int32_t where) {
+    const size_t bytes = spinor_bytes(s);
+    void* dst = where == KD_HOST ? s->work : psi;
+    const int blocks = grid_blocks(s->P, 256) < 4096 ? grid_blocks(s->P, 256) : 4096;
+    if (s->prec == KD_FP64) k_permute<double><<<blocks, 256, 0, s->stream>>>((const double*)s->psi, (double*)dst, s->P, 0);
+    else k_permute<float><<<blocks, 256, 0, s->stream>>>((const float*)s->psi, (float*)dst, s->P, 0);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    if (where == KD_HOST) {
+        KD_CUDA(cudaMemcpyAsync(psi, s->work, bytes, cudaMemcpyDeviceToHost, s->stream));
+        KD_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    return KD_OK;
+}
+
+}  // namespace
+
+// =================================================================== public ABI ===
+
+extern "C" {
+
+const char* kd_last_error(void) { return g_err.c_str(); }
+
+int kd_version(void) { return 100; }
+
+int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field, int32_t precision,
+              void* cuda_stream, kd_sim** out) {
+    g_err.clear();
+    if (!units || !grid || !field || !out) return fail(KD_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (precision != KD_FP64 && precision != KD_FP32) return fail(KD_ERR_ARG, "precision must be KD_FP64 or KD_FP32");
+    if (!pow2_in_range(grid->nx) || !pow2_in_range(grid->ny))
+        return fail(KD_ERR_UNSUPPORTED_SIZE, "nx=%d ny=%d: need powers of two in [4, 4096]", grid->nx, grid->ny);
+    if (!(grid->x_max > grid->x_min) || !(grid->y_max > grid->y_min) || !isfinite(grid->x_min) ||
+        !isfinite(grid->x_max) || !isfinite(grid->y_min) || !isfinite(grid->y_max))
+        return fail(KD_ERR_ARG, "box limits must be finite with max > min");
+    if (!(units->m > 0) || !(units->c > 0) || !(units->hbar > 0) || !isfinite(units->m) ||
+        !isfinite(units->c) || !isfinite(units->hbar))
+        return fail(KD_ERR_ARG, "units m, c, hbar must be positive and finite");
+    if (field->kind < KD_FIELD_NONE || field->kind > KD_FIELD_GAUSS) return fail(KD_ERR_ARG, "unknown field kind %d", field->kind);
+    const double fv[] = {field->a0, field->k_L, field->epsilon, field->env_T, field->phase0,
+                         field->p_shift_x, field->p_shift_y, field->box_vy};
+    for (double v : fv)
+        if (!isfinite(v)) return fail(KD_ERR_ARG, "field parameters must be finite");
+    if (field->kind != KD_FIELD_NONE && !(field->k_L > 0)) return fail(KD_ERR_ARG, "k_L must be > 0");
+    if (field->kind == KD_FIELD_GAUSS && !(field->epsilon > 0)) return fail(KD_ERR_ARG, "epsilon must be > 0 for the Gaussian beam");
+    if (field->env_T < 0) return fail(KD_ERR_ARG, "env_T must be >= 0");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(KD_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    int ndev = 0;
+    e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev <= 0) return fail(KD_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+
+    kd_sim* s = new kd_sim();
+    s->u = *units;
+    s->g = *grid;
+    s->f = *field;
+    s->prec = precision;
+    s->tsize = precision == KD_FP64 ? 8 : 4;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->device = dev;
+    s->lx = ilog2(grid->nx);
+    s->ly = ilog2(grid->ny);
+    s->P = (size_t)grid->nx * grid->ny;
+    auto bail = [&](int rc) { kd_destroy(s); return rc; };
+#define KD_ALLOC(ptr, bytes)                                                             \
+    do {                                                                                 \
+        cudaError_t ea_ = cudaMalloc((void**)&(ptr), (bytes));                           \
+        if (ea_ != cudaSuccess)                                                          \
+            return bail(fail(KD_ERR_NOMEM, "cudaMalloc(%zu): %s", (size_t)(bytes), cudaGetErrorString(ea_))); \
+    } while (0)
+    if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(KD_ERR_CUDA, "stream create failed"));
+    KD_ALLOC(s->psi, spinor_bytes(s));
+    KD_ALLOC(s->work, spinor_bytes(s));
+    KD_ALLOC(s->tw_x, (size_t)grid->nx * cbytes(s));
+    KD_ALLOC(s->tw_y, (size_t)grid->ny * cbytes(s));
+    KD_ALLOC(s->xtab, 6 * (size_t)grid->nx * s->tsize);
+    KD_ALLOC(s->kxtab, (size_t)grid->nx * s->tsize);
+    KD_ALLOC(s->kytab, 4 * (size_t)grid->ny * s->tsize);
+    KD_ALLOC(s->ktab, s->P * cbytes(s));
+    KD_ALLOC(s->clock, sizeof(Clock));
+    KD_ALLOC(s->rowsum, (size_t)grid->ny * sizeof(double));
+    KD_ALLOC(s->scalar, 4 * sizeof(double));
+    KD_ALLOC(s->status, sizeof(int));
+#undef KD_ALLOC
+    if (cudaMemset(s->psi, 0, spinor_bytes(s)) != cudaSuccess ||
+        cudaMemset(s->clock, 0, sizeof(Clock)) != cudaSuccess ||
+        cudaMemset(s->scalar, 0, 4 * sizeof(double)) != cudaSuccess ||
+        cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess)
+        return bail(fail(KD_ERR_CUDA, "memset failed"));
+    int rc = precision == KD_FP64 ? upload_tables_t<double>(s) : upload_tables_t<float>(s);
+    if (rc) return bail(rc);
+    // first launch of every sweep shape outside any stream capture (sets kernel
+    // attributes); the spinor is zero, so this leaves it unchanged
+    const int shapes[3] = {SHAPE_F1, SHAPE_F2, SHAPE_F1F2};
+    for (int ax = 0; ax < 2; ++ax)
+        for (int sh : shapes) {
+            cudaError_t el = sweep(s, ax, sh, OP_NONE, s->psi, s->psi, 0, 0.0);
+            if (el != cudaSuccess) return bail(fail(KD_ERR_CUDA, "sweep launch: %s", cudaGetErrorString(el)));
+        }
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(KD_ERR_CUDA, "device synchronize failed"));
+    *out = s;
+    return KD_OK;
+}
+
+void kd_destroy(kd_sim* s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->stream);
+    clear_graphs(s);
+    void* bufs[] = {s->psi, s->work, s->tw_x, s->tw_y, s->xtab, s->kxtab, s->kytab, s->ktab,
+                    s->clock, s->steps, s->rowsum, s->md, s->scalar, s->obs_dev, s->status};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    delete s;
+}
+
+int kd_set_spinor(kd_sim* s, const void* psi, int32_t where) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!psi || (where != KD_HOST && where != KD_DEVICE)) return fail(KD_ERR_ARG, "bad spinor pointer or where");
+    return copy_in(s, psi, where);
+}
+
+int kd_get_spinor(kd_sim* s, void* psi, int32_t where) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!psi || (where != KD_HOST && where != KD_DEVICE)) return fail(KD_ERR_ARG, "bad spinor pointer or where");
+    return copy_out(s, psi, where);
+}
+
+int kd_set_time(kd_sim* s, double t) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!isfinite(t)) return fail(KD_ERR_ARG, "time must be finite");
+    s->t0 = t;
+    s->step = 0;
+    clear_graphs(s);
+    return KD_OK;
+}
+
+int kd_get_time(kd_sim* s, double* t, int64_t* steps_done) {
+    if (!s) return fail(KD_ERR_ARG, "null simulation");
+    if (t) *t = s->t0 + (double)s->step * s->dt_clock;
+    if (steps_done) *steps_done = s->step;
+    return KD_OK;
+}
+
+int kd_set_obs_spec(kd_sim* s, const kd_obs_spec* spec) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!spec) return fail(KD_ERR_ARG, "null spec");
+    ObsWin w;
+    rc = make_window(s, spec, &w);
+    if (rc) return rc;
+    s->spec = *spec;
+    s->has_spec = true;
+    clear_graphs(s);
+    return KD_OK;
+}
+
+int kd_set_watchdog(kd_sim* s, double tol) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!(tol == tol)) return fail(KD_ERR_ARG, "tol is NaN");
+    s->watch_tol = tol;
+    clear_graphs(s);
+    return KD_OK;
+}
+
+int kd_init_packet(kd_sim* s, const kd_packet* pk) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!pk) return fail(KD_ERR_ARG, "null packet");
+    if (!(pk->sigma_p > 0) || !isfinite(pk->sigma_p) || !isfinite(pk->p0x) || !isfinite(pk->p0y) ||
+        !isfinite(pk->r0x) || !isfinite(pk->r0y))
+        return fail(KD_ERR_ARG, "packet parameters must be finite with sigma_p > 0");
+    if ((pk->spin != 1 && pk->spin != -1) || (pk->basis != 0 && pk->basis != 1))
+        return fail(KD_ERR_ARG, "spin must be +-1 and basis 0 or 1");
+    const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
+    const double dpy = s->u.hbar * 2.0 * kPi / (s->g.y_max - s->g.y_min);
+    const double mc2 = s->u.m * s->u.c * s->u.c;
+    const double rx = pk->r0x - s->g.x_min, ry = pk->r0y - s->g.y_min;
+    if (s->prec == KD_FP64)
+        k_packet<double><<<grid_blocks(s->P, 256), 256, 0, s->stream>>>(
+            (double*)s->psi, s->g.nx, s->g.ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y, pk->p0x,
+            pk->p0y, rx, ry, pk->sigma_p, pk->spin, pk->basis, s->u.c, mc2, s->u.hbar);
+    else
+        k_packet<float><<<grid_blocks(s->P, 256), 256, 0, s->stream>>>(
+            (float*)s->psi, s->g.nx, s->g.ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y, pk->p0x,
+            pk->p0y, rx, ry, pk->sigma_p, pk->spin, pk->basis, s->u.c, mc2, s->u.hbar);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F2, OP_NONE, s->psi, s->psi, 0, 0.0));
+    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F1, OP_NONE, s->psi, s->psi, 0, 0.0));
+    rc = rowsum_launch(s, s->psi);
+    if (rc) return rc;
+    k_norm<<<1, 256, 0, s->stream>>>(s->rowsum, s->g.ny, dxdy(s), s->scalar, 0);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    const size_t nreal = s->P * 8;
+    if (s->prec == KD_FP64) k_scale_by_norm<double><<<1024, 256, 0, s->stream>>>((double*)s->psi, nreal, s->scalar);
+    else k_scale_by_norm<float><<<1024, 256, 0, s->stream>>>((float*)s->psi, nreal, s->scalar);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    KD_CUDA(cudaStreamSynchronize(s->stream));
+    s->t0 = 0.0;
+    s->step = 0;
+    const double hk = s->u.hbar * s->f.k_L;
+    kd_obs_spec sp{};
+    sp.p_in_x = pk->p0x; sp.p_in_y = pk->p0y;
+    sp.p_diff_x = pk->p0x + 2.0 * hk; sp.p_diff_y = pk->p0y;
+    sp.target_x = sp.p_diff_x; sp.target_y = sp.p_diff_y;
+    sp.half_width = 0.5 * hk;
+    sp.basis = pk->basis;
+    ObsWin w;
+    if (make_window(s, &sp, &w) == KD_OK) { s->spec = sp; s->has_spec = true; }
+    else { s->has_spec = false; g_err.clear(); }
+    clear_graphs(s);
+    return KD_OK;
+}
+
+int kd_step(kd_sim* s, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs_out,
+            int64_t obs_cap, int64_t* n_obs) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (n_obs) *n_obs = 0;
+    if (!(dt > 0) || !isfinite(dt)) return fail(KD_ERR_ARG, "dt must be positive and finite");
+    if (nsteps < 0 || obs_every < 0 || obs_cap < 0) return fail(KD_ERR_ARG, "negative count");
+    if (nsteps > (int64_t)1 << 40) return fail(KD_ERR_ARG, "nsteps too large");
+    if (obs_every > 0 && obs_cap > 0 && !obs_out) return fail(KD_ERR_ARG, "obs_out is null");
+    if (obs_every > 0 && !s->has_spec) return fail(KD_ERR_ARG, "no observation spec: call kd_init_packet or kd_set_obs_spec");
+    if (nsteps == 0) return KD_OK;
+    ObsWin w{};
+    if (obs_every > 0) {
+        rc = make_window(s, &s->spec, &w);
+        if (rc) return rc;
+    }
+    // rebase the clock when dt changes: t = t0 + step * dt
+    if (dt != s->dt_clock) {
+        s->t0 = s->t0 + (double)s->step * s->dt_clock;
+        s->step = 0;
+        s->dt_clock = dt;
+    }
+    if (dt != s->ktab_dt) {
+        rc = build_dt_tables(s, dt);
+        if (rc) return rc;
+        clear_graphs(s);
+    }
+    const int64_t nobs = obs_every > 0 ? nsteps / obs_every : 0;
+    const int64_t cap = nobs < obs_cap ? nobs : obs_cap;
+    rc = ensure_steps(s, nsteps);
+    if (rc) return rc;
+    if (nobs > 0) {
+        rc = ensure_obs(s, cap > 0 ? cap : 1);
+        if (!rc) rc = ensure_md(s);
+        if (rc) return rc;
+    }
+    if (obs_every != s->graph_obs_every || cap != s->graph_obs_cap || dt != s->graph_dt ||
+        s->t0 != s->graph_t0 || memcmp(&w, &s->graph_win, sizeof w) != 0) {
+        clear_graphs(s);
+        s->graph_obs_every = obs_every;
+        s->graph_obs_cap = cap;
+        s->graph_dt = dt;
+        s->graph_t0 = s->t0;
+        s->graph_win = w;
+    }
+    const double omega = s->u.c * s->f.k_L;
+    k_step_scalars<<<grid_blocks((size_t)nsteps + 1, 256), 256, 0, s->stream>>>(
+        s->steps, nsteps, s->t0, s->step, dt, s->f.a0, omega, s->f.phase0, s->f.env_T, s->f.box_vy);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    k_set_clock<<<1, 1, 0, s->stream>>>(s->clock, 0);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    if (nobs > 0) {
+        KD_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), s->stream));
+        if (s->watch_tol > 0) {
+            rc = rowsum_launch(s, s->psi);
+            if (rc) return rc;
+            k_norm<<<1, 256, 0, s->stream>>>(s->rowsum, s->g.ny, dxdy(s), s->scalar, 1);
+            KD_CUDA(cudaGetLastError());
+    ++s->launches;
+        }
+    }
+    // opening half step of the first step (t_0)
+    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_POTENTIAL, s->psi, s->psi, 0, 0.5 * dt));
+    const int64_t chunk_n = obs_every > 0 ? obs_every : 64;
+    int64_t done = 0;
+    while (done < nsteps) {
+        const int64_t left = nsteps - done;
+        const int chunk = (int)(left < chunk_n ? left : chunk_n);
+        const bool last = done + chunk == nsteps;
+        const bool obs = obs_every > 0 && chunk == obs_every;
+        if (chunk <= 4096) {
+            rc = run_chunk(s, dt, chunk, last, obs, w, obs_every, cap);
+        } else {  // very long chunks without observations run in pieces of 64
+            rc = KD_OK;
+            int64_t rem = chunk;
+            while (rem > 0 && rc == KD_OK) {
+                const int c2 = (int)(rem < 64 ? rem : 64);
+                rc = run_chunk(s, dt, c2, last && rem == c2, false, w, obs_every, cap);
+                rem -= c2;
+            }
+        }
+        if (rc) return rc;
+        done += chunk;
+    }
+    s->step += nsteps;
+    if (nobs > 0) {
+        if (cap > 0) KD_CUDA(cudaMemcpyAsync(obs_out, s->obs_dev, cap * sizeof(kd_obs), cudaMemcpyDeviceToHost, s->stream));
+        int st = 0;
+        KD_CUDA(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+        KD_CUDA(cudaStreamSynchronize(s->stream));
+        if (n_obs) *n_obs = nobs;
+        if (st & 1) return fail(KD_ERR_NONFINITE, "non-finite norm observed");
+        if (st & 2) return fail(KD_ERR_NORM_DRIFT, "norm drift beyond %g", s->watch_tol);
+    }
+    return KD_OK;
+}
+
+int kd_observe(kd_sim* s, const kd_obs_spec* spec, kd_obs* out) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!out) return fail(KD_ERR_ARG, "null output");
+    if (!spec && !s->has_spec) return fail(KD_ERR_ARG, "no observation spec");
+    const kd_obs_spec* sp = spec ? spec : &s->spec;
+    ObsWin w;
+    rc = make_window(s, sp, &w);
+    if (rc) return rc;
+    rc = ensure_obs(s, 1);
+    if (rc) return rc;
+    const double t = s->t0 + (double)s->step * s->dt_clock;
+    rc = observe_launch(s, w, sp->basis, false, 0, t, 1, 1, s->obs_dev);
+    if (rc) return rc;
+    KD_CUDA(cudaMemcpyAsync(out, s->obs_dev, sizeof(kd_obs), cudaMemcpyDeviceToHost, s->stream));
+    KD_CUDA(cudaStreamSynchronize(s->stream));
+    return KD_OK;
+}
+
+int kd_get_momentum_density(kd_sim* s, int32_t basis, double* out, int32_t where) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!out || (where != KD_HOST && where != KD_DEVICE) || (basis != 0 && basis != 1))
+        return fail(KD_ERR_ARG, "bad output pointer, where or basis");
+    double* dst = out;
+    if (where == KD_HOST) {
+        rc = ensure_md(s);
+        if (rc) return rc;
+        dst = s->md;
+    }
+    rc = momentum_density_launch(s, basis, dst);
+    if (rc) return rc;
+    if (where == KD_HOST) {
+        KD_CUDA(cudaMemcpyAsync(out, s->md, s->P * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        KD_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    return KD_OK;
+}
+
+int kd_get_density_x(kd_sim* s, double* out, int32_t where) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!out || (where != KD_HOST && where != KD_DEVICE)) return fail(KD_ERR_ARG, "bad output pointer or where");
+    double* dst = out;
+    if (where == KD_HOST) {
+        rc = ensure_md(s);
+        if (rc) return rc;
+        dst = s->md;
+    }
+    const double dy = (s->g.y_max - s->g.y_min) / s->g.ny;
+    if (s->prec == KD_FP64) k_density_x<double><<<grid_blocks(s->g.nx, 128), 128, 0, s->stream>>>((const double*)s->psi, s->g.nx, s->g.ny, dy, dst);
+    else k_density_x<float><<<grid_blocks(s->g.nx, 128), 128, 0, s->stream>>>((const float*)s->psi, s->g.nx, s->g.ny, dy, dst);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    if (where == KD_HOST) {
+        KD_CUDA(cudaMemcpyAsync(out, dst, s->g.nx * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        KD_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    return KD_OK;
+}
+
+int kd_bench_sweep(kd_sim* s, int32_t kind, int32_t reps) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if ((kind != 0 && kind != 1) || reps < 0) return fail(KD_ERR_ARG, "kind must be 0 or 1, reps >= 0");
+    if (s->ktab_dt == 0.0 || !s->steps) return fail(KD_ERR_ARG, "call kd_step once before kd_bench_sweep");
+    k_set_clock<<<1, 1, 0, s->stream>>>(s->clock, 0);
+    KD_CUDA(cudaGetLastError());
+    for (int32_t i = 0; i < reps; ++i) {
+        if (kind == 0) KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F1F2, OP_POTENTIAL, s->psi, s->psi, 0, s->ktab_dt));
+        else KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F1F2, OP_KINETIC, s->psi, s->psi, 0, 0.0));
+    }
+    return KD_OK;
+}
+
+int kd_get_launch_count(kd_sim* s, int64_t* n) {
+    if (!s || !n) return fail(KD_ERR_ARG, "null argument");
+    *n = s->launches;
+    return KD_OK;
+}
+
+int kd_get_state(kd_sim* s, void* buf, size_t* size) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!size) return fail(KD_ERR_ARG, "null size");
+    const size_t need = sizeof(StateHeader) + spinor_bytes(s);
+    if (!buf || *size < need) {
+        *size = need;
+        return buf ? fail(KD_ERR_ARG, "buffer too small (%zu < %zu)", *size, need) : KD_OK;
+    }
+    StateHeader h{};
+    h.magic = 0x3153444bu;  // "KDS1"
+    h.version = 1;
+    h.nx = s->g.nx;
+    h.ny = s->g.ny;
+    h.prec = s->prec;
+    h.hash = param_hash(s);
+    h.t0 = s->t0;
+    h.dt_clock = s->dt_clock;
+    h.step = s->step;
+    h.payload = spinor_bytes(s);
+    memcpy(buf, &h, sizeof h);
+    rc = copy_out(s, (char*)buf + sizeof h, KD_HOST);
+    if (rc) return rc;
+    *size = need;
+    return KD_OK;
+}
+
+int kd_set_state(kd_sim* s, const void* buf, size_t size) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!buf || size < sizeof(StateHeader)) return fail(KD_ERR_ARG, "state buffer too small");
+    StateHeader h;
+    memcpy(&h, buf, sizeof h);
+    if (h.magic != 0x3153444bu || h.version != 1) return fail(KD_ERR_STATE_MISMATCH, "not a kd state");
+    if (h.nx != s->g.nx || h.ny != s->g.ny || h.prec != s->prec || h.hash != param_hash(s) ||
+        h.payload != spinor_bytes(s) || size < sizeof h + h.payload)
+        return fail(KD_ERR_STATE_MISMATCH, "state was taken from a different simulation");
+    rc = copy_in(s, (const char*)buf + sizeof h, KD_HOST);
+    if (rc) return rc;
+    s->t0 = h.t0;
+    s->dt_clock = h.dt_clock;
+    s->step = h.step;
+    clear_graphs(s);
+    return KD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// kd_internal.h -- declarations shared by the host API (kd_api.cu) and the sweep kernels
+// (kd_sweep_f32.cu, kd_sweep_f64.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kd {
+
+// Internal component order of a grid point: (psi1, psi4, psi2, psi3).  In 2D with
+// A = (A_x, A_y) and p = (p_x, p_y) both alpha.A and alpha.p + beta couple only
+// psi1 <-> psi4 and psi2 <-> psi3, so each pair is contiguous: pair 0 = (psi1, psi4),
+// pair 1 = (psi2, psi3).  Pair 1's 2x2 generators are pair 0's with the y component
+// negated.
+__host__ __device__ constexpr int perm_to_dirac(int s) {  // internal slot -> Dirac component
+    return s == 0 ? 0 : (s == 1 ? 3 : (s == 2 ? 1 : 2));
+}
+
+enum SweepAxis { AXIS_X = 0, AXIS_Y = 1 };
+// FFT presence: FFT1 runs before the pointwise op, FFT2 after it.  On the x axis FFT1
+// is inverse and FFT2 forward; on the y axis FFT1 is forward and FFT2 inverse.
+enum SweepShape { SHAPE_F2 = 1, SHAPE_F1 = 2, SHAPE_F1F2 = 3 };
+enum SweepOp { OP_NONE = 0, OP_POTENTIAL = 1, OP_KINETIC = 2 };
+
+// Per-step scalars, FP64, written once per kd_step by a small kernel.
+struct StepScalars {
+    double t;   // time of the step boundary
+    double s;   // a0 f(t) sin(omega t + phase0): common factor of the standing wave
+    double Y;   // co-moving box offset box_vy t
+    double pad;
+};
+
+// Device clock: absolute step index of the state and the index at the start of the
+// current kd_step call.  Kernels index StepScalars with (step - base) + n_local.
+struct Clock {
+    long long step;
+    long long base;
+};
+
+struct SweepArgs {
+    const void* in;
+    void* out;
+    const void* tw;       // N complex (precision of the sweep), exp(-2 pi i m / N)
+    int nx, ny;
+    int op;
+    // potential (x sweep)
+    const Clock* clock;
+    const StepScalars* steps;
+    int n_local;
+    int kind, longitudinal;
+    double kappa;         // tau m c^2 / hbar for this sweep (tau = dt or dt/2)
+    double eps4;          // 4 epsilon (longitudinal amplitude factor)
+    double y_min, dy;
+    const void* xtab;     // [6][nx] per-x field table, precision of the sweep
+    // kinetic (y sweep)
+    const void* ktab;     // [ny][nx] (C/P, c S/P) pairs
+    const void* kxtab;    // [nx] pi_x
+    const void* kytab;    // [ny] (pi_y, cos, sin of the frame phase, pad)
+    double mc;            // m c
+};
+
+// Launches one sweep; returns cudaSuccess or the launch error.  logn in [2, 12].
+cudaError_t launch_sweep_f32(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_f64(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
+
+}  // namespace kd

@@ -1,0 +1,468 @@
+// kd_sweep.cuh -- the fused sweep kernels of the FFT split-operator step (Sec. II.D of
+// arXiv 2307.01571) for sm_103a.
+//
+// One Strang step psi <- V_half(t_{n+1}) F^-1 K F V_half(t_n) psi is executed as two
+// passes over the spinor in HBM:
+//   x sweep: per row  -- inverse x-FFT, merged potential factor exp(-i dt V(t_n)/hbar)
+//            (closing half of step n-1 times opening half of step n, the same matrix),
+//            forward x-FFT;
+//   y sweep: per column tile -- forward y-FFT, kinetic factor, inverse y-FFT.
+// Between sweeps the state lives in (k_x, y) space.  The first and last x sweeps of a
+// run apply a true half step and only one of the two FFTs.
+//
+// FFT engine: Stockham autosort, radix 8/4/2, every thread owns E = 8 (FP32) or 4 (FP64)
+// elements of one line for all four spinor components in registers; butterflies run on
+// registers and stages exchange data through shared memory with an XOR swizzle that
+// keeps 16-byte accesses free of bank conflicts.  The last stage of the first FFT and the
+// first stage of the second FFT use the same radix and butterfly-to-thread map, so the
+// pointwise factor in between is applied straight on registers with no exchange, and the
+// first/last stages read/write global memory in natural order (coalesced, in place).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "kd_internal.h"
+
+namespace kd {
+
+#define KD_DI __device__ __forceinline__
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using t = float2; };
+template <> struct Cx<double> { using t = double2; };
+
+template <typename C> KD_DI C mk(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
+template <typename C> KD_DI C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> KD_DI C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> KD_DI C cmul(C a, C b) {
+    return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a times (DIR i)
+template <int DIR, typename C> KD_DI C mul_i(C a) {
+    return DIR > 0 ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+}
+
+// ------------------------------------------------------------ small DFTs ---------
+// In place on a[0], a[S], ..., output in natural order, X_k = sum_j a_j w^{jk},
+// w = exp(DIR 2 pi i / R).
+template <int DIR, int S, typename C> KD_DI void dft2(C* a) {
+    C t = a[0];
+    a[0] = cadd(t, a[S]);
+    a[S] = csub(t, a[S]);
+}
+
+template <int DIR, int S, typename C> KD_DI void dft4(C* a) {
+    C s02 = cadd(a[0], a[2 * S]), d02 = csub(a[0], a[2 * S]);
+    C s13 = cadd(a[S], a[3 * S]), d13 = csub(a[S], a[3 * S]);
+    C r = mul_i<DIR>(d13);
+    a[0] = cadd(s02, s13);
+    a[2 * S] = csub(s02, s13);
+    a[S] = cadd(d02, r);
+    a[3 * S] = csub(d02, r);
+}
+
+template <int DIR, int S, typename C> KD_DI void dft8(C* a) {
+    using T = decltype(C::x);
+    const T h = T(0.70710678118654752440084436210484903928);
+    C e[4] = {a[0], a[2 * S], a[4 * S], a[6 * S]};
+    C o[4] = {a[S], a[3 * S], a[5 * S], a[7 * S]};
+    dft4<DIR, 1>(e);
+    dft4<DIR, 1>(o);
+    // o_k *= w8^k, w8 = exp(DIR 2 pi i / 8)
+    o[1] = mk<C>((o[1].x - DIR * o[1].y) * h, (o[1].y + DIR * o[1].x) * h);
+    o[2] = mul_i<DIR>(o[2]);
+    o[3] = mk<C>((-o[3].x - DIR * o[3].y) * h, (-o[3].y + DIR * o[3].x) * h);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k * S] = cadd(e[k], o[k]);
+        a[(k + 4) * S] = csub(e[k], o[k]);
+    }
+}
+
+template <int R, int DIR, int S, typename C> KD_DI void dftR(C* a) {
+    if constexpr (R == 2) dft2<DIR, S>(a);
+    else if constexpr (R == 4) dft4<DIR, S>(a);
+    else dft8<DIR, S>(a);
+}
+
+// ------------------------------------------------------------- plan ---------------
+// Radix plan of an N = 2^logn point FFT with maximum radix 2^loge: as many radix-2^loge
+// stages as fit, the remainder as radix-4 or radix-2 stages.
+__host__ __device__ constexpr int plan_nst(int logn, int loge) {
+    return loge == 3 ? (logn % 3 == 0 ? logn / 3 : logn / 3 + 1)
+                     : (loge == 2 ? logn / 2 + logn % 2 : logn);
+}
+__host__ __device__ constexpr int plan_logr(int logn, int loge, int s) {
+    if (loge == 3) {
+        int q = logn / 3, r = logn % 3;
+        if (r == 0) return 3;
+        if (r == 1) return s < q - 1 ? 3 : 2;
+        return s < q ? 3 : 2;
+    }
+    if (loge == 2) return s < logn / 2 ? 2 : 1;
+    return 1;
+}
+__host__ __device__ constexpr int plan_logns(int logn, int loge, int s) {  // log2 of Ns before stage s
+    int a = 0;
+    for (int i = 0; i < s; ++i) a += plan_logr(logn, loge, i);
+    return a;
+}
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
+
+template <typename T, int LOGN, int AXIS> struct Cfg {
+    static constexpr bool F64 = sizeof(T) == 8;
+    static constexpr int N = 1 << LOGN;
+    static constexpr int NC = (F64 && LOGN >= 12) ? 2 : 4;      // components per CTA
+    static constexpr int LOGRMAX = F64 ? (NC == 2 ? 3 : 2) : 3;
+    static constexpr int LOGE = LOGN < LOGRMAX ? LOGN : LOGRMAX;
+    static constexpr int E = 1 << LOGE;                          // elements per thread
+    static constexpr int TF = N / E;                             // threads per line
+    static constexpr int BATCH = TF >= 256 ? 1 : 256 / TF;       // lines per CTA
+    static constexpr int THREADS = TF * BATCH;
+    static constexpr int CPP = F64 ? 1 : 2;                      // complex per 16-byte unit
+    static constexpr int NPL = NC / CPP;                         // units per point in the CTA
+    static constexpr int UPP = 4 / CPP;                          // units per point in memory
+    static constexpr int NPAIRS = 4 / NC;
+    static constexpr int NST = plan_nst(LOGN, LOGE);
+    static constexpr int SMEM_BYTES = (NST > 1 ? BATCH * NPL * N * 16 : 16);
+    // lanes of one 8-lane (128-byte) shared-memory wavefront cover 2^LOGG consecutive
+    // butterflies
+    static constexpr int LOGG =
+        cmin(LOGN, AXIS == AXIS_X ? 3 : cmax(0, 3 - clog2(BATCH)));
+};
+
+// XOR swizzle of element index i for the exchange after a stage with Ns = 2^la and
+// radix 2^lb: spreads the 2^g butterflies of a wavefront over distinct 16-byte bank
+// groups for the strided write and keeps the contiguous read conflict-free.
+template <int LA, int LB, int G> KD_DI int swz(int i) {
+    if constexpr (LA >= G) {
+        return i;
+    } else {
+        constexpr int SH = cmax(G, LA + LB);
+        constexpr int W = cmin(LB, G - LA);
+        return i ^ (((i >> SH) & ((1 << W) - 1)) << LA);
+    }
+}
+
+// ------------------------------------------------------- register <-> 16 B --------
+template <typename T> struct Unit;
+template <> struct Unit<float> {
+    using U = float4;
+    KD_DI static U pack(const float2* c) { return make_float4(c[0].x, c[0].y, c[1].x, c[1].y); }
+    KD_DI static void unpack(U u, float2* c) { c[0] = make_float2(u.x, u.y); c[1] = make_float2(u.z, u.w); }
+};
+template <> struct Unit<double> {
+    using U = double2;
+    KD_DI static U pack(const double2* c) { return c[0]; }
+    KD_DI static void unpack(U u, double2* c) { c[0] = u; }
+};
+
+// ------------------------------------------------------------- the kernel ---------
+template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
+    using Cf = Cfg<T, LOGN, AXIS>;
+    using C = typename Cx<T>::t;
+    using U = typename Unit<T>::U;
+    static constexpr int N = Cf::N, E = Cf::E, TF = Cf::TF, NC = Cf::NC, NST = Cf::NST;
+    static constexpr int NPL = Cf::NPL, CPP = Cf::CPP, BATCH = Cf::BATCH;
+    // direction of the first and second FFT (forward = -1)
+    static constexpr int DIR1 = AXIS == AXIS_X ? +1 : -1;
+    static constexpr int DIR2 = -DIR1;
+    static constexpr bool HAS1 = (SHAPE & SHAPE_F1) != 0;
+    static constexpr bool HAS2 = (SHAPE & SHAPE_F2) != 0;
+    // radix (log) of the stage that sits next to the pointwise op in both FFTs
+    static constexpr int LR_OP = plan_logr(LOGN, Cf::LOGE, NST - 1);
+    static constexpr int LR_LOAD = HAS1 ? plan_logr(LOGN, Cf::LOGE, 0) : LR_OP;
+    static constexpr int LR_STORE = HAS2 ? plan_logr(LOGN, Cf::LOGE, 0) : LR_OP;
+
+    struct Ctx {
+        int jt, bb, line, pair;
+        bool valid;
+        U* sm;
+    };
+
+    KD_DI static int point_of(const SweepArgs& a, int line, int idx) {
+        return AXIS == AXIS_X ? line * a.nx + idx : idx * a.nx + line;
+    }
+    KD_DI static int sm_addr(const Ctx& c, int p, int sw) {
+        return AXIS == AXIS_X ? (c.bb * NPL + p) * N + sw : (p * N + sw) * BATCH + c.bb;
+    }
+
+    // registers hold slots e = m*R + r for butterfly j = jt + m*TF, element index
+    // j + r*N/R (the input layout of a stage with radix R = 2^LR)
+    template <int LR> KD_DI static void load(const SweepArgs& a, const Ctx& c, C* v) {
+        constexpr int R = 1 << LR;
+        const U* g = reinterpret_cast<const U*>(a.in);
+#pragma unroll
+        for (int m = 0; m < E / R; ++m)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                int idx = c.jt + m * TF + r * (N / R);
+                long long base = (long long)point_of(a, c.line, idx) * Cf::UPP + c.pair * NPL;
+#pragma unroll
+                for (int p = 0; p < NPL; ++p) {
+                    U u;
+                    if (c.valid) u = g[base + p];
+                    else u = U{};
+                    Unit<T>::unpack(u, v + (m * R + r) * NC + p * CPP);
+                }
+            }
+    }
+    template <int LR> KD_DI static void store(const SweepArgs& a, const Ctx& c, const C* v) {
+        constexpr int R = 1 << LR;
+        U* g = reinterpret_cast<U*>(a.out);
+        if (!c.valid) return;
+#pragma unroll
+        for (int m = 0; m < E / R; ++m)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                int idx = c.jt + m * TF + r * (N / R);
+                long long base = (long long)point_of(a, c.line, idx) * Cf::UPP + c.pair * NPL;
+#pragma unroll
+                for (int p = 0; p < NPL; ++p) g[base + p] = Unit<T>::pack(v + (m * R + r) * NC + p * CPP);
+            }
+    }
+
+    // one Stockham stage: twiddle (Ns > 1) and radix-R butterflies on registers
+    template <int DIR, int LR, int LNS> KD_DI static void stage(const SweepArgs& a, const Ctx& c, C* v) {
+        constexpr int R = 1 << LR;
+        const C* tw = reinterpret_cast<const C*>(a.tw);
+#pragma unroll
+        for (int m = 0; m < E / R; ++m) {
+            C* b = v + m * R * NC;
+            if constexpr (LNS > 0) {
+                int j = c.jt + m * TF;
+                int k = j & ((1 << LNS) - 1);
+                constexpr int STEP = N >> (LNS + LR);  // N / (Ns R)
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = __ldg(tw + r * k * STEP);
+                    if (DIR > 0) w.y = -w.y;
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) b[r * NC + q] = cmul(b[r * NC + q], w);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NC; ++q) dftR<R, DIR, NC>(b + q);
+        }
+    }
+
+    // shared-memory exchange from the output layout of stage (LA = log Ns, LB = log R)
+    // to the input layout of a stage with radix 2^LRN
+    template <int LA, int LB, int LRN> KD_DI static void exchange(const Ctx& c, C* v) {
+        constexpr int R = 1 << LB;
+        constexpr int RN = 1 << LRN;
+        constexpr int G = Cf::LOGG;
+#pragma unroll
+        for (int m = 0; m < E / R; ++m) {
+            int j = c.jt + m * TF;
+            int hi = ((j >> LA) << (LA + LB)) | (j & ((1 << LA) - 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                int sw = swz<LA, LB, G>(hi | (r << LA));
+#pragma unroll
+                for (int p = 0; p < NPL; ++p) c.sm[sm_addr(c, p, sw)] = Unit<T>::pack(v + (m * R + r) * NC + p * CPP);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < E / RN; ++m) {
+            int j = c.jt + m * TF;
+#pragma unroll
+            for (int r = 0; r < RN; ++r) {
+                int sw = swz<LA, LB, G>(j | (r << (LOGN - LRN)));
+#pragma unroll
+                for (int p = 0; p < NPL; ++p) Unit<T>::unpack(c.sm[sm_addr(c, p, sw)], v + (m * RN + r) * NC + p * CPP);
+            }
+        }
+        __syncthreads();
+    }
+
+    // FFT with stages in plan order (REV = false) or reversed plan order (REV = true)
+    template <int DIR, bool REV, int S> KD_DI static void fft(const SweepArgs& a, const Ctx& c, C* v) {
+        if constexpr (S < NST) {
+            constexpr int PS = REV ? NST - 1 - S : S;              // plan index of this stage
+            constexpr int LR = plan_logr(LOGN, Cf::LOGE, PS);
+            constexpr int LNS = REV ? LOGN - plan_logns(LOGN, Cf::LOGE, PS + 1)
+                                    : plan_logns(LOGN, Cf::LOGE, PS);
+            stage<DIR, LR, LNS>(a, c, v);
+            if constexpr (S + 1 < NST) {
+                constexpr int PN = REV ? NST - 2 - S : S + 1;
+                exchange<LNS, LR, plan_logr(LOGN, Cf::LOGE, PN)>(c, v);
+                fft<DIR, REV, S + 1>(a, c, v);
+            }
+        }
+    }
+
+    // --------------------------------------------------------- pointwise ops -------
+    // potential factor exp(-i tau V/hbar), V = -m c^2 alpha.a, on registers in the op
+    // layout (element index j + r N/R_op is the x index of the row)
+    KD_DI static void op_potential(const SweepArgs& a, const Ctx& c, C* v) {
+        if (a.kind == 0) return;
+        constexpr int R = 1 << LR_OP;
+        const Clock ck = *a.clock;
+        const StepScalars ss = a.steps[(ck.step - ck.base) + a.n_local];
+        const double yrow = a.y_min + (double)c.line * a.dy + ss.Y;
+        const T y = (T)yrow;
+        const T y2 = y * y;
+        const T st = (T)ss.s;
+        const T kap = (T)a.kappa;
+        const T* xt = reinterpret_cast<const T*>(a.xtab);
+        const int nx = a.nx;
+#pragma unroll
+        for (int m = 0; m < E / R; ++m)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int x = c.jt + m * TF + r * (N / R);
+                T ax, ay;
+                if (a.kind == 1) {
+                    ax = T(0);
+                    ay = T(-2) * st * __ldg(xt + x);
+                } else {
+                    const T th0 = __ldg(xt + x), zeta = __ldg(xt + nx + x), cc = __ldg(xt + 2 * nx + x);
+                    const T gw = __ldg(xt + 3 * nx + x), iw2 = __ldg(xt + 4 * nx + x);
+                    const T G = gw * exp(-y2 * iw2);
+                    const T th = th0 - cc * y2;
+                    ay = T(-2) * st * G * cos(th);
+                    ax = T(0);
+                    if (a.longitudinal) {
+                        const T invw = __ldg(xt + 5 * nx + x);
+                        ax = (T)a.eps4 * st * (y * invw) * G * sin(th + zeta);
+                    }
+                }
+                const T amag = sqrt(ax * ax + ay * ay);
+                const T th = kap * amag;
+                T sn, cs;
+                sincos_(th, &sn, &cs);
+                const T s = amag > T(0) ? sn / amag : kap;
+                C* e = v + (m * R + r) * NC;
+#pragma unroll
+                for (int q = 0; q < NC / 2; ++q) {
+                    const int pr = NC == 4 ? q : c.pair;
+                    const T sg = pr == 0 ? T(1) : T(-1);
+                    const C u = e[2 * q], l = e[2 * q + 1];
+                    const C q1 = mk<C>(s * sg * ay, s * ax);
+                    const C q2 = mk<C>(-s * sg * ay, s * ax);
+                    e[2 * q] = cadd(mk<C>(cs * u.x, cs * u.y), cmul(q1, l));
+                    e[2 * q + 1] = cadd(mk<C>(cs * l.x, cs * l.y), cmul(q2, u));
+                }
+            }
+    }
+
+    // kinetic factor [C - i S H0(pi)] e^{i phi_frame} / P on registers; element index is
+    // k_y, the line is k_x
+    KD_DI static void op_kinetic(const SweepArgs& a, const Ctx& c, C* v) {
+        constexpr int R = 1 << LR_OP;
+        const C* kt = reinterpret_cast<const C*>(a.ktab);
+        const T pix = __ldg(reinterpret_cast<const T*>(a.kxtab) + c.line);
+        const T mc = (T)a.mc;
+        using T4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
+        const T4* kyt = reinterpret_cast<const T4*>(a.kytab);
+#pragma unroll
+        for (int m = 0; m < E / R; ++m)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int ky = c.jt + m * TF + r * (N / R);
+                const C cs = __ldg(kt + (long long)ky * a.nx + c.line);
+                const T4 yv = kyt[ky];
+                const T Cp = cs.x, Sp = cs.y;
+                const T mcS = Sp * mc;
+                const C ph = mk<C>(yv.y, yv.z);
+                const C d1 = cmul(ph, mk<C>(Cp, -mcS));
+                const C d2 = cmul(ph, mk<C>(Cp, mcS));
+                C* e = v + (m * R + r) * NC;
+#pragma unroll
+                for (int q = 0; q < NC / 2; ++q) {
+                    const int pr = NC == 4 ? q : c.pair;
+                    const T sg = pr == 0 ? T(1) : T(-1);
+                    const C o1 = cmul(ph, mk<C>(-Sp * sg * yv.x, -Sp * pix));
+                    const C o2 = cmul(ph, mk<C>(Sp * sg * yv.x, -Sp * pix));
+                    const C u = e[2 * q], l = e[2 * q + 1];
+                    e[2 * q] = cadd(cmul(d1, u), cmul(o1, l));
+                    e[2 * q + 1] = cadd(cmul(d2, l), cmul(o2, u));
+                }
+            }
+    }
+
+    KD_DI static void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
+    KD_DI static void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+
+    KD_DI static void run(const SweepArgs& a) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        Ctx c;
+        const int tid = threadIdx.x;
+        if (AXIS == AXIS_X) { c.bb = tid / TF; c.jt = tid % TF; }
+        else { c.bb = tid % BATCH; c.jt = tid / BATCH; }
+        c.pair = NC == 2 ? (int)blockIdx.y : 0;
+        c.line = (int)blockIdx.x * BATCH + c.bb;
+        c.valid = c.line < (AXIS == AXIS_X ? a.ny : a.nx);
+        c.sm = reinterpret_cast<U*>(smem_raw);
+        C v[E * NC];
+        load<LR_LOAD>(a, c, v);
+        if constexpr (HAS1) fft<DIR1, false, 0>(a, c, v);
+        if (AXIS == AXIS_X && a.op == OP_POTENTIAL) op_potential(a, c, v);
+        if (AXIS == AXIS_Y && a.op == OP_KINETIC) op_kinetic(a, c, v);
+        if constexpr (HAS2) fft<DIR2, true, 0>(a, c, v);
+        store<LR_STORE>(a, c, v);
+    }
+};
+
+template <typename T, int LOGN, int AXIS, int SHAPE>
+__global__ void __launch_bounds__(Cfg<T, LOGN, AXIS>::THREADS)
+sweep_kernel(const SweepArgs a) {
+    Sweep<T, LOGN, AXIS, SHAPE>::run(a);
+}
+
+template <typename T, int LOGN, int AXIS, int SHAPE>
+cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
+    using Cf = Cfg<T, LOGN, AXIS>;
+    static bool attr_done = false;
+    auto k = sweep_kernel<T, LOGN, AXIS, SHAPE>;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              Cf::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const int lines = AXIS == AXIS_X ? a.ny : a.nx;
+    dim3 grid((lines + Cf::BATCH - 1) / Cf::BATCH, Cf::NPAIRS);
+    k<<<grid, Cf::THREADS, Cf::SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int AXIS, int SHAPE>
+cudaError_t launch_logn(int logn, const SweepArgs& a, cudaStream_t s) {
+    switch (logn) {
+        case 2: return launch_one<T, 2, AXIS, SHAPE>(a, s);
+        case 3: return launch_one<T, 3, AXIS, SHAPE>(a, s);
+        case 4: return launch_one<T, 4, AXIS, SHAPE>(a, s);
+        case 5: return launch_one<T, 5, AXIS, SHAPE>(a, s);
+        case 6: return launch_one<T, 6, AXIS, SHAPE>(a, s);
+        case 7: return launch_one<T, 7, AXIS, SHAPE>(a, s);
+        case 8: return launch_one<T, 8, AXIS, SHAPE>(a, s);
+        case 9: return launch_one<T, 9, AXIS, SHAPE>(a, s);
+        case 10: return launch_one<T, 10, AXIS, SHAPE>(a, s);
+        case 11: return launch_one<T, 11, AXIS, SHAPE>(a, s);
+        case 12: return launch_one<T, 12, AXIS, SHAPE>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t launch_sweep(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s) {
+    if (axis == AXIS_X) {
+        if (shape == SHAPE_F1F2) return launch_logn<T, AXIS_X, SHAPE_F1F2>(logn, a, s);
+        if (shape == SHAPE_F1) return launch_logn<T, AXIS_X, SHAPE_F1>(logn, a, s);
+        if (shape == SHAPE_F2) return launch_logn<T, AXIS_X, SHAPE_F2>(logn, a, s);
+    } else {
+        if (shape == SHAPE_F1F2) return launch_logn<T, AXIS_Y, SHAPE_F1F2>(logn, a, s);
+        if (shape == SHAPE_F1) return launch_logn<T, AXIS_Y, SHAPE_F1>(logn, a, s);
+        if (shape == SHAPE_F2) return launch_logn<T, AXIS_Y, SHAPE_F2>(logn, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace kd

@@ -1,0 +1,245 @@
+"""ctypes binding of ``libkd.so`` (C ABI in ``include/kd.h``).
+
+Argument marshalling only: every step of the split-operator path runs in the library's
+CUDA kernels.  The raw entry points are exported under their C names (``kd_create``,
+``kd_step``, ...); :class:`Sim` wraps them for numpy arrays and torch tensors.  There is
+no CPU fallback: importing this module raises if the library is missing, and
+``kd_create`` fails without a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkd.so")
+
+KD_OK = 0
+KD_ERR_ARG, KD_ERR_UNSUPPORTED_SIZE, KD_ERR_CUDA = -1, -2, -3
+KD_ERR_NONFINITE, KD_ERR_NORM_DRIFT, KD_ERR_TIMEOUT = -4, -5, -6
+KD_ERR_STATE_MISMATCH, KD_ERR_NOMEM = -7, -8
+KD_FP64, KD_FP32 = 0, 1
+KD_HOST, KD_DEVICE = 0, 1
+
+
+class KdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"kd error {code}: {msg}")
+        self.code = code
+
+
+class kd_units(C.Structure):
+    _fields_ = [("m", C.c_double), ("c", C.c_double), ("hbar", C.c_double), ("q", C.c_double)]
+
+
+class kd_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("x_min", C.c_double),
+                ("x_max", C.c_double), ("y_min", C.c_double), ("y_max", C.c_double)]
+
+
+class kd_field(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("longitudinal", C.c_int32), ("a0", C.c_double),
+                ("k_L", C.c_double), ("epsilon", C.c_double), ("env_T", C.c_double),
+                ("phase0", C.c_double), ("p_shift_x", C.c_double), ("p_shift_y", C.c_double),
+                ("box_vy", C.c_double)]
+
+
+class kd_packet(C.Structure):
+    _fields_ = [("p0x", C.c_double), ("p0y", C.c_double), ("r0x", C.c_double),
+                ("r0y", C.c_double), ("sigma_p", C.c_double), ("spin", C.c_int32),
+                ("basis", C.c_int32)]
+
+
+class kd_obs_spec(C.Structure):
+    _fields_ = [("p_in_x", C.c_double), ("p_in_y", C.c_double), ("p_diff_x", C.c_double),
+                ("p_diff_y", C.c_double), ("target_x", C.c_double), ("target_y", C.c_double),
+                ("half_width", C.c_double), ("basis", C.c_int32), ("pad_", C.c_int32)]
+
+
+OBS_FIELDS = ["t", "norm", "pop_in", "pop_diff", "cp_in", "cm_in", "cp_diff", "cm_diff",
+              "max_diff", "cp_max_diff", "cm_max_diff", "p_target", "cp_target", "cm_target"]
+
+
+class kd_obs(C.Structure):
+    _fields_ = [(n, C.c_double) for n in OBS_FIELDS]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                      "(the CUDA library is the only compute path)")
+_lib = C.CDLL(LIB_PATH)
+
+_vp, _P = C.c_void_p, C.POINTER
+_SIGS = {
+    "kd_create": (C.c_int, [_P(kd_units), _P(kd_grid), _P(kd_field), C.c_int32, _vp, _P(_vp)]),
+    "kd_init_packet": (C.c_int, [_vp, _P(kd_packet)]),
+    "kd_set_obs_spec": (C.c_int, [_vp, _P(kd_obs_spec)]),
+    "kd_set_spinor": (C.c_int, [_vp, _vp, C.c_int32]),
+    "kd_get_spinor": (C.c_int, [_vp, _vp, C.c_int32]),
+    "kd_set_time": (C.c_int, [_vp, C.c_double]),
+    "kd_get_time": (C.c_int, [_vp, _P(C.c_double), _P(C.c_int64)]),
+    "kd_step": (C.c_int, [_vp, C.c_double, C.c_int64, C.c_int64, _P(kd_obs), C.c_int64,
+                          _P(C.c_int64)]),
+    "kd_observe": (C.c_int, [_vp, _P(kd_obs_spec), _P(kd_obs)]),
+    "kd_get_momentum_density": (C.c_int, [_vp, C.c_int32, _vp, C.c_int32]),
+    "kd_get_density_x": (C.c_int, [_vp, _vp, C.c_int32]),
+    "kd_set_watchdog": (C.c_int, [_vp, C.c_double]),
+    "kd_get_state": (C.c_int, [_vp, _vp, _P(C.c_size_t)]),
+    "kd_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "kd_bench_sweep": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "kd_get_launch_count": (C.c_int, [_vp, _P(C.c_int64)]),
+    "kd_destroy": (None, [_vp]),
+    "kd_last_error": (C.c_char_p, []),
+    "kd_version": (C.c_int, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+    globals()[_name] = _fn
+
+EXPORTS = list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != KD_OK:
+        raise KdError(rc, kd_last_error().decode())
+
+
+def _fill(cls, obj):
+    s = cls()
+    for name, _ in cls._fields_:
+        if name != "pad_":
+            setattr(s, name, getattr(obj, name))
+    return s
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+class Sim:
+    """One simulation on the current CUDA device (see ``kd_create``)."""
+
+    def __init__(self, units: W.Units, grid: W.Grid, field: W.Field, precision: int = KD_FP64,
+                 stream: int | None = None):
+        self.units, self.grid, self.field, self.precision = units, grid, field, precision
+        self.cdtype = np.complex128 if precision == KD_FP64 else np.complex64
+        h = _vp()
+        _check(kd_create(C.byref(_fill(kd_units, units)), C.byref(_fill(kd_grid, grid)),
+                         C.byref(_fill(kd_field, field)), precision,
+                         _vp(stream) if stream else None, C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, wl: W.Workload, stream: int | None = None) -> "Sim":
+        return cls(wl.units, wl.grid, wl.field, wl.precision, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            kd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.grid.ny, self.grid.nx, 4)
+
+    def init_packet(self, packet: W.Packet):
+        _check(kd_init_packet(self._h, C.byref(_fill(kd_packet, packet))))
+
+    def set_obs_spec(self, spec: W.ObsSpec):
+        _check(kd_set_obs_spec(self._h, C.byref(_fill(kd_obs_spec, spec))))
+
+    def set_spinor(self, psi):
+        if _is_torch(psi):
+            assert psi.is_contiguous() and tuple(psi.shape) == self.shape
+            where = KD_DEVICE if psi.is_cuda else KD_HOST
+            _check(kd_set_spinor(self._h, _vp(psi.data_ptr()), where))
+        else:
+            a = np.ascontiguousarray(psi, dtype=self.cdtype)
+            assert a.shape == self.shape
+            _check(kd_set_spinor(self._h, a.ctypes.data_as(_vp), KD_HOST))
+
+    def get_spinor(self, out=None):
+        if out is not None and _is_torch(out):
+            assert out.is_contiguous() and tuple(out.shape) == self.shape
+            _check(kd_get_spinor(self._h, _vp(out.data_ptr()), KD_DEVICE if out.is_cuda else KD_HOST))
+            return out
+        a = np.empty(self.shape, self.cdtype) if out is None else out
+        _check(kd_get_spinor(self._h, a.ctypes.data_as(_vp), KD_HOST))
+        return a
+
+    def set_time(self, t: float):
+        _check(kd_set_time(self._h, t))
+
+    def get_time(self):
+        t, n = C.c_double(), C.c_int64()
+        _check(kd_get_time(self._h, C.byref(t), C.byref(n)))
+        return t.value, n.value
+
+    def step(self, dt: float, nsteps: int, obs_every: int = 0, obs_cap: int | None = None):
+        nobs = nsteps // obs_every if obs_every > 0 else 0
+        cap = nobs if obs_cap is None else obs_cap
+        buf = (kd_obs * max(cap, 1))()
+        n = C.c_int64()
+        _check(kd_step(self._h, dt, nsteps, obs_every, buf if cap > 0 else None, cap,
+                       C.byref(n)))
+        return [{k: getattr(buf[i], k) for k in OBS_FIELDS} for i in range(min(n.value, cap))]
+
+    def observe(self, spec: W.ObsSpec | None = None) -> dict:
+        o = kd_obs()
+        _check(kd_observe(self._h, C.byref(_fill(kd_obs_spec, spec)) if spec else None,
+                          C.byref(o)))
+        return {k: getattr(o, k) for k in OBS_FIELDS}
+
+    def momentum_density(self, basis: int = 0) -> np.ndarray:
+        out = np.empty((self.grid.ny, self.grid.nx, 3), np.float64)
+        _check(kd_get_momentum_density(self._h, basis, out.ctypes.data_as(_vp), KD_HOST))
+        return out
+
+    def density_x(self) -> np.ndarray:
+        out = np.empty(self.grid.nx, np.float64)
+        _check(kd_get_density_x(self._h, out.ctypes.data_as(_vp), KD_HOST))
+        return out
+
+    def set_watchdog(self, tol: float):
+        _check(kd_set_watchdog(self._h, tol))
+
+    def bench_sweep(self, kind: int, reps: int):
+        _check(kd_bench_sweep(self._h, kind, reps))
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        _check(kd_get_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    def get_state(self) -> bytes:
+        n = C.c_size_t(0)
+        _check(kd_get_state(self._h, None, C.byref(n)))
+        buf = (C.c_char * n.value)()
+        _check(kd_get_state(self._h, buf, C.byref(n)))
+        return bytes(buf)
+
+    def set_state(self, blob: bytes):
+        buf = (C.c_char * len(blob)).from_buffer_copy(blob)
+        _check(kd_set_state(self._h, buf, len(blob)))

@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on identical seeded
+inputs.  Tolerances: FP64 max |psi_gpu - psi_oracle| <= 1e-10 max |psi| and norm drift
+<= 1e-12; FP32 <= 1e-4 max |psi| and norm drift <= 1e-6 (per grid-point arithmetic in
+FP32 with FP64-built tables: a 2D FFT round trip of log2 P stages adds ~1e-7 relative
+per step)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_01571_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL = {0: 1e-10, 1: 1e-4}
+NORM_TOL = {0: 1e-12, 1: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def kd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2307_01571_gb300 import _build
+    _build.build()
+    from paper_2307_01571_gb300 import kd as mod
+    return mod
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.complex128) - b)) / np.max(np.abs(b)))
+
+
+SIZES = [(4, 4), (8, 4), (4, 16), (16, 8), (64, 32), (32, 128), (128, 128), (256, 64),
+         (8, 512), (1024, 8), (2048, 4), (4, 2048), (4096, 4), (4, 4096)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nx,ny", SIZES)
+def test_packet_init(kd, prec, nx, ny):
+    wl = W.small(nx, ny, W.GAUSS, units=W.ATOMIC)
+    ref = oracle.init_packet(wl.units, wl.grid, wl.field, wl.packet)
+    with kd.Sim(wl.units, wl.grid, wl.field, prec) as sim:
+        sim.init_packet(wl.packet)
+        got = sim.get_spinor()
+    assert rel(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nx,ny", [(4, 4), (16, 8), (64, 32), (128, 256), (1024, 8), (4, 1024)])
+def test_momentum_density_of_random_spinor(kd, prec, nx, ny):
+    wl = W.small(nx, ny, W.PLANE, units=W.NATURAL)
+    psi = W.random_spinor(nx, ny, 100 + nx + ny)
+    ref = oracle.momentum_density(wl.units, wl.grid, wl.field, psi, basis=0)
+    with kd.Sim(wl.units, wl.grid, wl.field, prec) as sim:
+        sim.set_spinor(psi)
+        got = sim.momentum_density(0)
+        back = sim.get_spinor()
+        dens = sim.density_x()
+    assert np.max(np.abs(got - ref)) <= TOL[prec] * np.max(ref)
+    assert rel(back, psi) <= (0 if prec == 0 else 1e-7)
+    dref = oracle.density_x(wl.grid, psi)
+    assert np.max(np.abs(dens - dref)) <= (1e-14 if prec == 0 else 1e-6) * np.max(dref)
+
+
+FIELDS = {
+    "none": dict(kind=W.NONE),
+    "plane": dict(kind=W.PLANE),
+    "plane_env": dict(kind=W.PLANE, env=True),
+    "gauss": dict(kind=W.GAUSS, longitudinal=1),
+    "gauss_transverse_static": dict(kind=W.GAUSS, longitudinal=0, box_vy=0.0),
+}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("fname", list(FIELDS))
+@pytest.mark.parametrize("nx,ny", [(4, 4), (32, 16), (64, 128), (256, 32)])
+def test_step_random_spinor(kd, prec, fname, nx, ny):
+    wl = W.small(nx, ny, units=W.ATOMIC, a0=0.4, nsteps=6, **FIELDS[fname])
+    psi = W.random_spinor(nx, ny, 7 * nx + ny)
+    ref = oracle.step(wl.units, wl.grid, wl.field, psi, 0.0, wl.dt, wl.nsteps)
+    with kd.Sim(wl.units, wl.grid, wl.field, prec) as sim:
+        sim.set_spinor(psi)
+        sim.step(wl.dt, wl.nsteps)
+        got = sim.get_spinor()
+        t, n = sim.get_time()
+    assert rel(got, ref) <= TOL[prec]
+    assert n == wl.nsteps and abs(t - wl.nsteps * wl.dt) <= 1e-15 * t
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("units", ["atomic", "natural"])
+def test_packet_run_with_observables(kd, prec, units):
+    u = W.ATOMIC if units == "atomic" else W.NATURAL
+    wl = W.small(128, 64, W.GAUSS, units=u, a0=0.2, nsteps=60)
+    g, f, pk = wl.grid, wl.field, wl.packet
+    spec = W.default_obs_spec(u, f, pk)
+    psi = oracle.init_packet(u, g, f, pk)
+    refs = []
+    t = 0.0
+    for _ in range(3):
+        psi = oracle.step(u, g, f, psi, t, wl.dt, 20)
+        t += 20 * wl.dt
+        refs.append(oracle.observe(u, g, f, spec, psi, t))
+    with kd.Sim(u, g, f, prec) as sim:
+        sim.init_packet(pk)
+        obs = sim.step(wl.dt, 60, obs_every=20)
+        got = sim.get_spinor()
+        final = sim.observe()
+    assert rel(got, psi) <= TOL[prec]
+    assert len(obs) == 3
+    for o, r in zip(obs, refs):
+        assert abs(o["t"] - r["t"]) <= 1e-15 * r["t"]
+        for k in W.ObsSpec.__dataclass_fields__:
+            pass
+        for k, v in r.items():
+            if k == "t":
+                continue
+            assert abs(o[k] - v) <= TOL[prec] * max(1.0, abs(v)), (k, o[k], v)
+    for k, v in refs[-1].items():
+        assert abs(final[k] - v) <= TOL[prec] * max(1.0, abs(v)), (k, final[k], v)
+
+
+def test_c1_against_stored_oracle_fixture(kd):
+    with open(os.path.join(HERE, "golden", "c1_oracle_obs.json")) as fh:
+        stored = json.load(fh)
+    wl = W.c1()
+    with kd.Sim.from_workload(wl) as sim:
+        sim.init_packet(wl.packet)
+        obs = sim.step(wl.dt, wl.nsteps, obs_every=100)
+    assert len(obs) == 2
+    for o, r in zip(obs, stored["obs"]):
+        for k, v in r.items():
+            assert abs(o[k] - v) <= 1e-10 * max(1.0, abs(v)), (k, o[k], v)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_1024x512_gaussian_beam(kd, prec):
+    """The benchmark's grid and launch path (graph-captured kd_step with observations):
+    a few steps compared element by element with the oracle."""
+    wl = W.c2(precision=prec, nsteps=4)
+    u, g, f, pk = wl.units, wl.grid, wl.field, wl.packet
+    ref = oracle.init_packet(u, g, f, pk)
+    ref = oracle.step(u, g, f, ref, 0.0, wl.dt, 4)
+    spec = W.default_obs_spec(u, f, pk)
+    oref = oracle.observe(u, g, f, spec, ref, 4 * wl.dt)
+    with kd.Sim.from_workload(wl) as sim:
+        sim.init_packet(pk)
+        obs = sim.step(wl.dt, 4, obs_every=2)
+        got = sim.get_spinor()
+    assert rel(got, ref) <= TOL[prec]
+    for k, v in oref.items():
+        assert abs(obs[-1][k] - v) <= TOL[prec] * max(1.0, abs(v)), k
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_norm_drift_2000_steps(kd, prec):
+    """Unitarity over the full benchmark run (a property that holds at any size)."""
+    wl = W.c2(precision=prec)
+    with kd.Sim.from_workload(wl) as sim:
+        sim.init_packet(wl.packet)
+        n0 = sim.observe()["norm"]
+        obs = sim.step(wl.dt, wl.nsteps, obs_every=wl.obs_every)
+    drift = max(abs(o["norm"] - n0) for o in obs)
+    assert abs(n0 - 1.0) <= NORM_TOL[prec]
+    assert drift <= NORM_TOL[prec], drift
+    assert all(math.isfinite(o["pop_diff"]) for o in obs)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bitwise_determinism_and_checkpoint_resume(kd, prec):
+    wl = W.small(256, 128, W.GAUSS, units=W.ATOMIC, a0=0.3)
+    outs = []
+    for split in (None, 13):
+        with kd.Sim.from_workload(wl.with_(precision=prec)) as sim:
+            sim.init_packet(wl.packet)
+            if split is None:
+                sim.step(wl.dt, 13)
+                sim.step(wl.dt, 17)
+            else:
+                sim.step(wl.dt, split)
+                blob = sim.get_state()
+                with kd.Sim.from_workload(wl.with_(precision=prec)) as sim2:
+                    sim2.set_state(blob)
+                    assert sim2.get_time()[1] == split
+                    sim2.step(wl.dt, 30 - split)
+                    outs.append(sim2.get_spinor())
+                continue
+            outs.append(sim.get_spinor())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_errors_are_reported_not_raised_on_device(kd):
+    wl = W.small(32, 32, W.GAUSS, units=W.ATOMIC)
+    with kd.Sim.from_workload(wl) as sim:
+        sim.init_packet(wl.packet)
+        # non-finite input is caught by the observation watchdog
+        psi = sim.get_spinor()
+        psi[3, 5, 1] = np.nan
+        sim.set_spinor(psi)
+        with pytest.raises(kd.KdError) as e:
+            sim.step(wl.dt, 4, obs_every=2)
+        assert e.value.code == kd.KD_ERR_NONFINITE
+        sim.init_packet(wl.packet)
+        sim.set_watchdog(1e-300)
+        with pytest.raises(kd.KdError) as e:
+            sim.step(wl.dt, 4, obs_every=2)
+        assert e.value.code in (kd.KD_ERR_NORM_DRIFT,)
+        sim.set_watchdog(0.0)
+        sim.step(wl.dt, 4, obs_every=2)
+        bad = W.ObsSpec(1e9, 0, 0, 0, 0, 0, 0.1)
+        with pytest.raises(kd.KdError) as e:
+            sim.set_obs_spec(bad)
+        assert e.value.code == kd.KD_ERR_ARG
+        with pytest.raises(kd.KdError):
+            sim.step(-1.0, 3)
+        blob = sim.get_state()
+    with kd.Sim.from_workload(wl.with_(precision=1)) as other:
+        with pytest.raises(kd.KdError) as e:
+            other.set_state(blob)
+        assert e.value.code == kd.KD_ERR_STATE_MISMATCH
+
+
+def test_device_pointers_and_torch_stream(kd):
+    import torch
+    wl = W.small(64, 64, W.GAUSS, units=W.ATOMIC)
+    psi = W.random_spinor(64, 64, 5)
+    ref = oracle.step(wl.units, wl.grid, wl.field, psi, 0.0, wl.dt, 3)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        dev = torch.from_numpy(psi).cuda()
+        with kd.Sim(wl.units, wl.grid, wl.field, 0, stream=s.cuda_stream) as sim:
+            sim.set_spinor(dev)
+            sim.step(wl.dt, 3)
+            out = torch.empty_like(dev)
+            sim.get_spinor(out)
+            s.synchronize()
+    assert rel(out.cpu().numpy(), ref) <= 1e-10
