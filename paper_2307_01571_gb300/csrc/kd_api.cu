@@ -124,23 +124,53 @@ void clear_graphs(kd_sim* s) {
 
 // ---------------------------------------------------------------- small kernels ---
 
-// Kinetic table: C/P and c S/P with C = cos(E dt/hbar), S = sin(E dt/hbar)/E, E from
-// the relativistic energy-momentum relation (Sec. II.B), pi = canonical + p_shift.
-// FP64 throughout; rounded once to the sweep precision.
+// Kinetic table: (C - 1)/P and c S/P with C = cos(E dt/hbar) (C - 1 = -2 sin^2(E dt/2hbar)
+// kept as a small number), S = sin(E dt/hbar)/E, E from the relativistic energy-momentum
+// relation (Sec. II.B), pi = canonical + p_shift.  FP64 throughout; rounded once to the
+// sweep precision.
 template <typename T>
 __global__ void k_ktab(T* out, int nx, int ny, double dpx, double dpy, double shx, double shy,
-                       double c, double mc2, double hbar, double dt) {
+                       double c, double mc2, double hbar, double dt, const T* kxtab,
+                       const T* kytab, double mc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx * ny) return;
     const int kx = i % nx, ky = i / nx;
     const double px = dpx * (kx < nx / 2 ? kx : kx - nx) + shx;
     const double py = dpy * (ky < ny / 2 ? ky : ky - ny) + shy;
     const double E = sqrt(mc2 * mc2 + c * c * (px * px + py * py));
-    double sn, cs;
-    sincos(E * dt / hbar, &sn, &cs);
-    const double invP = 1.0 / ((double)nx * (double)ny);
-    out[2 * i] = (T)(cs * invP);
-    out[2 * i + 1] = (T)(c * sn / E * invP);
+    double sh, ch;
+    sincos(0.5 * E * dt / hbar, &sh, &ch);
+    const double P = (double)nx * (double)ny;
+    const double a = -2.0 * sh * sh / P, b = c * (2.0 * sh * ch) / E / P;
+    if (sizeof(T) == 8) {
+        out[2 * i] = (T)a;
+        out[2 * i + 1] = (T)b;
+        return;
+    }
+    // FP32: of the pairs within 3 ulps of the rounded (a, b), take the one whose factor
+    // 1/P + a - i b G, G = H0/c built from the same rounded m c, pi_x, pi_y that the sweep
+    // uses, is closest to unitary: (1 + P a)^2 + (P b)^2 |G|^2 = 1, ties broken by the
+    // closer rotation angle.  Plain rounding leaves a coherent per-step norm error of
+    // order (E dt)^2 2^-24 at every k, which adds up over thousands of steps.
+    const double gx = (double)kxtab[kx], gy = (double)kytab[4 * ky], gm = (double)(T)mc;
+    const double G = sqrt(gm * gm + gx * gx + gy * gy);
+    const float a0 = (float)a, b0 = (float)b;
+    const double ang0 = atan2(P * b * E / c, 1.0 + P * a);
+    float ba = a0, bb = b0;
+    double best = 1e300;
+    float ai = a0;
+    for (int k = 0; k < 3; ++k) ai = nextafterf(ai, -INFINITY);
+    for (int da = -3; da <= 3; ++da, ai = nextafterf(ai, INFINITY)) {
+        float bi = b0;
+        for (int k = 0; k < 3; ++k) bi = nextafterf(bi, -INFINITY);
+        for (int db = -3; db <= 3; ++db, bi = nextafterf(bi, INFINITY)) {
+            const double x = 1.0 + P * (double)ai, y = P * (double)bi * G;
+            const double g = fabs(x * x + y * y - 1.0) + 1e-3 * fabs(atan2(y, x) - ang0);
+            if (g < best) { best = g; ba = ai; bb = bi; }
+        }
+    }
+    out[2 * i] = (T)ba;
+    out[2 * i + 1] = (T)bb;
 }
 
 // Time-dependent scalars of the standing wave for the steps of one kd_step call:
@@ -167,14 +197,24 @@ __global__ void k_step_scalars(StepScalars* out, int64_t n, double t0, int64_t s
 __global__ void k_set_clock(Clock* c, long long step) { c->step = step; c->base = step; }
 __global__ void k_advance_clock(Clock* c, int n) { c->step += n; }
 
-// Per-row sum of |psi|^2 (fixed-order tree: bitwise reproducible).
+// Real offset of internal slot s (0..3) of a point in the pair-plane layout
+// [pair][P][2] complex: slot s = 2 pair + index within the pair.
+__host__ __device__ inline size_t slot_off(size_t P, size_t point, int s) {
+    return ((size_t)(s >> 1) * P + point) * 4 + 2 * (s & 1);
+}
+
+// Per-row sum of |psi|^2 over both pair planes (fixed-order tree: bitwise reproducible).
 template <typename T>
-__global__ void k_rowsum(const T* psi, int nx, double* rowsum) {
+__global__ void k_rowsum(const T* psi, int nx, int ny, double* rowsum) {
     __shared__ double red[256];
     const int row = blockIdx.x;
-    const T* p = psi + (size_t)row * nx * 8;
+    const size_t P = (size_t)nx * ny;
     double acc = 0.0;
-    for (int i = threadIdx.x; i < nx * 8; i += blockDim.x) acc += (double)p[i] * (double)p[i];
+    for (int i = threadIdx.x; i < nx * 8; i += blockDim.x) {
+        const int pair = i / (nx * 4), k = i % (nx * 4);
+        const double v = (double)psi[(pair * P + (size_t)row * nx) * 4 + k];
+        acc += v * v;
+    }
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -190,10 +230,13 @@ __global__ void k_density_x(const T* psi, int nx, int ny, double dy, double* out
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nx) return;
     double acc = 0.0;
+    const size_t P = (size_t)nx * ny;
     for (int y = 0; y < ny; ++y) {
-        const T* p = psi + ((size_t)y * nx + x) * 8;
         double s = 0.0;
-        for (int i = 0; i < 8; ++i) s += (double)p[i] * (double)p[i];
+        for (int pair = 0; pair < 2; ++pair) {
+            const T* p = psi + (pair * P + (size_t)y * nx + x) * 4;
+            for (int i = 0; i < 4; ++i) s += (double)p[i] * (double)p[i];
+        }
         acc += s;
     }
     out[x] = acc * dy;
@@ -266,8 +309,9 @@ __global__ void k_packet(T* psi, int nx, int ny, double dpx, double dpy, double 
     bispinor(c, mc2, pix, piy, spin, basis, u);
     for (int s = 0; s < 4; ++s) {
         const double2 uu = u[perm_to_dirac(s)];
-        psi[(size_t)i * 8 + 2 * s] = (T)(mag * (uu.x * cs - uu.y * sn));
-        psi[(size_t)i * 8 + 2 * s + 1] = (T)(mag * (uu.x * sn + uu.y * cs));
+        const size_t o = slot_off((size_t)nx * ny, i, s);
+        psi[o] = (T)(mag * (uu.x * cs - uu.y * sn));
+        psi[o + 1] = (T)(mag * (uu.x * sn + uu.y * cs));
     }
 }
 
@@ -283,8 +327,10 @@ __global__ void k_momentum_density(const T* phi, int nx, int ny, double dpx, dou
     const double pix = dpx * (kx < nx / 2 ? kx : kx - nx) + shx;
     const double piy = dpy * (ky < ny / 2 ? ky : ky - ny) + shy;
     double2 f[4];
-    for (int s = 0; s < 4; ++s)
-        f[perm_to_dirac(s)] = make_double2((double)phi[(size_t)i * 8 + 2 * s], (double)phi[(size_t)i * 8 + 2 * s + 1]);
+    for (int s = 0; s < 4; ++s) {
+        const size_t o = slot_off((size_t)nx * ny, i, s);
+        f[perm_to_dirac(s)] = make_double2((double)phi[o], (double)phi[o + 1]);
+    }
     double p2 = 0.0;
     for (int d = 0; d < 4; ++d) p2 += f[d].x * f[d].x + f[d].y * f[d].y;
     double cpm[2];
@@ -376,17 +422,16 @@ __global__ void k_obs_reduce(const double* rowsum, const double* md, int nx, int
     }
 }
 
-// Layout conversion between the ABI's Dirac order and the internal (psi1, psi4, psi2, psi3).
+// Layout conversion between the ABI's [P][4] Dirac order and the internal pair planes.
 template <typename T>
 __global__ void k_permute(const T* in, T* out, size_t npts, int to_internal) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npts;
          i += (size_t)gridDim.x * blockDim.x) {
-        T v[8];
-        for (int k = 0; k < 8; ++k) v[k] = in[i * 8 + k];
         for (int s = 0; s < 4; ++s) {
-            const int d = perm_to_dirac(s);
-            if (to_internal) { out[i * 8 + 2 * s] = v[2 * d]; out[i * 8 + 2 * s + 1] = v[2 * d + 1]; }
-            else { out[i * 8 + 2 * d] = v[2 * s]; out[i * 8 + 2 * d + 1] = v[2 * s + 1]; }
+            const size_t o = slot_off(npts, i, s);
+            const size_t d = i * 8 + 2 * perm_to_dirac(s);
+            if (to_internal) { out[o] = in[d]; out[o + 1] = in[d + 1]; }
+            else { out[d] = in[o]; out[d + 1] = in[o + 1]; }
         }
     }
 }
@@ -397,39 +442,47 @@ int grid_blocks(size_t n, int threads) { return (int)((n + threads - 1) / thread
 
 template <typename T> int upload_tables_t(kd_sim* s) {
     const int nx = s->g.nx, ny = s->g.ny;
-    // twiddles exp(-2 pi i m / N), FP64 then rounded
+    // twiddles exp(-2 pi i m / N) from FP64; FP32 entries are hi + lo pairs
+    // (c_hi, s_hi, c_lo, s_lo) so that the sweeps apply them to ~1e-15
     for (int ax = 0; ax < 2; ++ax) {
         const int n = ax == 0 ? nx : ny;
-        std::vector<T> tw(2 * n);
+        const int stride = sizeof(T) == 4 ? 4 : 2;
+        std::vector<T> tw(stride * (size_t)n, (T)0);
         for (int m = 0; m < n; ++m) {
             const double a = 2.0 * kPi * m / n;
-            tw[2 * m] = (T)cos(a);
-            tw[2 * m + 1] = (T)(-sin(a));
+            const double c = cos(a), sn = -sin(a);
+            tw[stride * m] = (T)c;
+            tw[stride * m + 1] = (T)sn;
+            if (stride == 4) {
+                tw[stride * m + 2] = (T)(c - (double)(T)c);
+                tw[stride * m + 3] = (T)(sn - (double)(T)sn);
+            }
         }
         KD_CUDA(cudaMemcpy(ax == 0 ? s->tw_x : s->tw_y, tw.data(), tw.size() * sizeof(T),
                            cudaMemcpyHostToDevice));
     }
-    // per-x field table (Eqs. Equation_of_Gaussian_beam, Phase_of_Gaussian_beam and w(x)):
-    // theta0 = (-k x + atan(x/x_R)) mod 2 pi, zeta = atan(x/x_R), x/(x_R w^2), w0/w, 1/w^2,
-    // 1/w; for the plane wave slot 0 holds cos(k x).
-    std::vector<T> xt(6 * (size_t)nx, (T)0);
+    // per-x field table (Eqs. Equation_of_Gaussian_beam, Phase_of_Gaussian_beam and w(x)),
+    // 8 entries per column: Theta0 = (-k x + zeta) mod 2 pi, x/(x_R w^2), w0/w, 1/w^2, 1/w,
+    // cos zeta, sin zeta (zeta = atan(x/x_R)), cos k x (plane wave)
+    std::vector<T> xt(8 * (size_t)nx, (T)0);
     const double dx = (s->g.x_max - s->g.x_min) / nx;
     const double k = s->f.k_L;
     for (int i = 0; i < nx; ++i) {
         const double x = s->g.x_min + i * dx;
-        if (s->f.kind == KD_FIELD_PLANE) {
-            xt[i] = (T)cos(k * x);
-        } else if (s->f.kind == KD_FIELD_GAUSS) {
+        T* e = xt.data() + 8 * (size_t)i;
+        e[7] = (T)cos(k * x);
+        if (s->f.kind == KD_FIELD_GAUSS) {
             const double w0 = 1.0 / (k * s->f.epsilon);
             const double xR = k * w0 * w0 / 2.0;
             const double w = w0 * sqrt(1.0 + x * x / (xR * xR));
             const double zeta = atan(x / xR);
-            xt[i] = (T)remainder(-k * x + zeta, 2.0 * kPi);
-            xt[nx + i] = (T)zeta;
-            xt[2 * nx + i] = (T)(x / (xR * w * w));
-            xt[3 * nx + i] = (T)(w0 / w);
-            xt[4 * nx + i] = (T)(1.0 / (w * w));
-            xt[5 * nx + i] = (T)(1.0 / w);
+            e[0] = (T)remainder(-k * x + zeta, 2.0 * kPi);
+            e[1] = (T)(x / (xR * w * w));
+            e[2] = (T)(w0 / w);
+            e[3] = (T)(1.0 / (w * w));
+            e[4] = (T)(1.0 / w);
+            e[5] = (T)cos(zeta);
+            e[6] = (T)sin(zeta);
         }
     }
     KD_CUDA(cudaMemcpy(s->xtab, xt.data(), xt.size() * sizeof(T), cudaMemcpyHostToDevice));
@@ -443,26 +496,49 @@ template <typename T> int upload_tables_t(kd_sim* s) {
 
 // Tables that depend on dt: the kinetic table (device, FP64) and the per-row
 // (pi_y, cos, sin of the frame phase box_vy p_y dt / hbar).
+// Rounded (cos(ph) - 1, sin(ph)) with |1 + f| = 1 as closely as the precision allows:
+// for FP32 the pair within 3 ulps of the rounded values with the smallest modulus error.
+template <typename T> void unit_phase(double ph, T* fx, T* fy) {
+    const double sh = sin(0.5 * ph);
+    const double x = -2.0 * sh * sh, y = sin(ph);
+    *fx = (T)x;
+    *fy = (T)y;
+    if (sizeof(T) != 4) return;
+    double best = 1e300;
+    float xi = (float)x;
+    for (int k = 0; k < 3; ++k) xi = nextafterf(xi, -INFINITY);
+    for (int dx = -3; dx <= 3; ++dx, xi = nextafterf(xi, INFINITY)) {
+        float yi = (float)y;
+        for (int k = 0; k < 3; ++k) yi = nextafterf(yi, -INFINITY);
+        for (int dy = -3; dy <= 3; ++dy, yi = nextafterf(yi, INFINITY)) {
+            const double g = fabs(2.0 * xi + (double)xi * xi + (double)yi * yi) +
+                             1e-3 * fabs(atan2((double)yi, 1.0 + xi) - ph);
+            if (g < best) { best = g; *fx = (T)xi; *fy = (T)yi; }
+        }
+    }
+}
+
+// Tables that depend on dt: the per-row (pi_y, cos(phi) - 1, sin(phi)) of the frame phase
+// phi = box_vy p_y dt / hbar and the kinetic table (device, FP64).
 template <typename T> int build_dt_tables_t(kd_sim* s, double dt) {
     const int nx = s->g.nx, ny = s->g.ny;
     const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
     const double dpy = s->u.hbar * 2.0 * kPi / (s->g.y_max - s->g.y_min);
     const double mc2 = s->u.m * s->u.c * s->u.c;
-    k_ktab<T><<<grid_blocks(s->P, 256), 256, 0, s->stream>>>(
-        (T*)s->ktab, nx, ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y, s->u.c, mc2, s->u.hbar, dt);
-    KD_CUDA(cudaGetLastError());
-    ++s->launches;
     std::vector<T> ky(4 * (size_t)ny);
     for (int j = 0; j < ny; ++j) {
         const double py = dpy * signed_index(j, ny);
-        const double ph = s->f.box_vy * py * dt / s->u.hbar;
         ky[4 * j] = (T)(py + s->f.p_shift_y);
-        ky[4 * j + 1] = (T)cos(ph);
-        ky[4 * j + 2] = (T)sin(ph);
+        unit_phase<T>(s->f.box_vy * py * dt / s->u.hbar, &ky[4 * j + 1], &ky[4 * j + 2]);
         ky[4 * j + 3] = (T)0;
     }
     KD_CUDA(cudaMemcpyAsync(s->kytab, ky.data(), ky.size() * sizeof(T), cudaMemcpyHostToDevice,
                             s->stream));
+    k_ktab<T><<<grid_blocks(s->P, 256), 256, 0, s->stream>>>(
+        (T*)s->ktab, nx, ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y, s->u.c, mc2, s->u.hbar, dt,
+        (const T*)s->kxtab, (const T*)s->kytab, s->u.m * s->u.c);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
     KD_CUDA(cudaStreamSynchronize(s->stream));
     s->ktab_dt = dt;
     return KD_OK;
@@ -509,8 +585,8 @@ cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* 
     } while (0)
 
 int rowsum_launch(kd_sim* s, const void* psi) {
-    if (s->prec == KD_FP64) k_rowsum<double><<<s->g.ny, 256, 0, s->stream>>>((const double*)psi, s->g.nx, s->rowsum);
-    else k_rowsum<float><<<s->g.ny, 256, 0, s->stream>>>((const float*)psi, s->g.nx, s->rowsum);
+    if (s->prec == KD_FP64) k_rowsum<double><<<s->g.ny, 256, 0, s->stream>>>((const double*)psi, s->g.nx, s->g.ny, s->rowsum);
+    else k_rowsum<float><<<s->g.ny, 256, 0, s->stream>>>((const float*)psi, s->g.nx, s->g.ny, s->rowsum);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
     return KD_OK;
@@ -798,9 +874,9 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
         return bail(fail(KD_ERR_CUDA, "stream create failed"));
     KD_ALLOC(s->psi, spinor_bytes(s));
     KD_ALLOC(s->work, spinor_bytes(s));
-    KD_ALLOC(s->tw_x, (size_t)grid->nx * cbytes(s));
-    KD_ALLOC(s->tw_y, (size_t)grid->ny * cbytes(s));
-    KD_ALLOC(s->xtab, 6 * (size_t)grid->nx * s->tsize);
+    KD_ALLOC(s->tw_x, (size_t)grid->nx * 16);
+    KD_ALLOC(s->tw_y, (size_t)grid->ny * 16);
+    KD_ALLOC(s->xtab, 8 * (size_t)grid->nx * s->tsize);
     KD_ALLOC(s->kxtab, (size_t)grid->nx * s->tsize);
     KD_ALLOC(s->kytab, 4 * (size_t)grid->ny * s->tsize);
     KD_ALLOC(s->ktab, s->P * cbytes(s));

@@ -6,11 +6,11 @@
 
 namespace kd {
 
-// Internal component order of a grid point: (psi1, psi4, psi2, psi3).  In 2D with
+// Internal spinor layout: two pair planes [pair][ny][nx][2] complex.  In 2D with
 // A = (A_x, A_y) and p = (p_x, p_y) both alpha.A and alpha.p + beta couple only
-// psi1 <-> psi4 and psi2 <-> psi3, so each pair is contiguous: pair 0 = (psi1, psi4),
-// pair 1 = (psi2, psi3).  Pair 1's 2x2 generators are pair 0's with the y component
-// negated.
+// psi1 <-> psi4 and psi2 <-> psi3, so the problem splits exactly into pair 0 = (psi1, psi4)
+// and pair 1 = (psi2, psi3); internal slot s = 2 pair + index within the pair.  Pair 1's
+// 2x2 generators are pair 0's with the y component negated.
 __host__ __device__ constexpr int perm_to_dirac(int s) {  // internal slot -> Dirac component
     return s == 0 ? 0 : (s == 1 ? 3 : (s == 2 ? 1 : 2));
 }
@@ -39,7 +39,8 @@ struct Clock {
 struct SweepArgs {
     const void* in;
     void* out;
-    const void* tw;       // N complex (precision of the sweep), exp(-2 pi i m / N)
+    const void* tw;       // N twiddles exp(-2 pi i m / N): double2 (FP64) or float4
+                          // (c, s, d, 0) with |(c, s)| (1 + d) = 1 (FP32)
     int nx, ny;
     int op;
     // potential (x sweep)
@@ -50,7 +51,8 @@ struct SweepArgs {
     double kappa;         // tau m c^2 / hbar for this sweep (tau = dt or dt/2)
     double eps4;          // 4 epsilon (longitudinal amplitude factor)
     double y_min, dy;
-    const void* xtab;     // [6][nx] per-x field table, precision of the sweep
+    const void* xtab;     // [nx][8] per-x field table, precision of the sweep:
+                          // (Theta0, x/(x_R w^2), w0/w, 1/w^2, 1/w, cos zeta, sin zeta, cos k x)
     // kinetic (y sweep)
     const void* ktab;     // [ny][nx] (C/P, c S/P) pairs
     const void* kxtab;    // [nx] pi_x

@@ -63,17 +63,26 @@ template <int DIR, int S, typename C> KD_DI void dft4(C* a) {
     a[3 * S] = csub(d02, r);
 }
 
+// multiply by 1/sqrt(2) as a hi + lo pair: a single rounded constant would make every
+// radix-8 butterfly shrink the norm of two of its eight inputs by 2 h^2 - 1 (about 4e-8
+// in FP32), a bias that accumulates over thousands of steps
+template <typename T> KD_DI T mul_rsqrt2(T x) {
+    if constexpr (sizeof(T) == 4) {
+        return fmaf(x, 0.707106769084930419921875f, x * 1.2101617e-08f);
+    } else {
+        return fma(x, 0.70710678118654757, x * -4.8336466567264567e-17);
+    }
+}
+
 template <int DIR, int S, typename C> KD_DI void dft8(C* a) {
-    using T = decltype(C::x);
-    const T h = T(0.70710678118654752440084436210484903928);
     C e[4] = {a[0], a[2 * S], a[4 * S], a[6 * S]};
     C o[4] = {a[S], a[3 * S], a[5 * S], a[7 * S]};
     dft4<DIR, 1>(e);
     dft4<DIR, 1>(o);
     // o_k *= w8^k, w8 = exp(DIR 2 pi i / 8)
-    o[1] = mk<C>((o[1].x - DIR * o[1].y) * h, (o[1].y + DIR * o[1].x) * h);
+    o[1] = mk<C>(mul_rsqrt2(o[1].x - DIR * o[1].y), mul_rsqrt2(o[1].y + DIR * o[1].x));
     o[2] = mul_i<DIR>(o[2]);
-    o[3] = mk<C>((-o[3].x - DIR * o[3].y) * h, (-o[3].y + DIR * o[3].x) * h);
+    o[3] = mk<C>(mul_rsqrt2(-o[3].x - DIR * o[3].y), mul_rsqrt2(-o[3].y + DIR * o[3].x));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         a[k * S] = cadd(e[k], o[k]);
@@ -116,16 +125,24 @@ __host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v
 template <typename T, int LOGN, int AXIS> struct Cfg {
     static constexpr bool F64 = sizeof(T) == 8;
     static constexpr int N = 1 << LOGN;
-    static constexpr int NC = (F64 && LOGN >= 12) ? 2 : 4;      // components per CTA
+    // components per CTA: FP32 CTAs own one 2x2 pair (twice the resident warps at half
+    // the registers); FP64 CTAs own both pairs so the costly FP64 field is evaluated once
+    static constexpr int NC = (!F64 || LOGN >= 12) ? 2 : 4;
     static constexpr int LOGRMAX = F64 ? (NC == 2 ? 3 : 2) : 3;
     static constexpr int LOGE = LOGN < LOGRMAX ? LOGN : LOGRMAX;
     static constexpr int E = 1 << LOGE;                          // elements per thread
     static constexpr int TF = N / E;                             // threads per line
-    static constexpr int BATCH = TF >= 256 ? 1 : 256 / TF;       // lines per CTA
+    // lines per CTA: rows are batched up to 128 threads; column tiles take 256 threads
+    // and at least 4 (FP32) or 2 (FP64) columns, i.e. >= 64 contiguous bytes per tile
+    // row, within 512 threads
+    static constexpr int MINB = F64 ? 2 : 4;
+    static constexpr int BATCH = AXIS == AXIS_X ? cmax(1, 128 / TF)
+                                                : (TF * MINB > 512 ? cmax(1, 512 / TF)
+                                                                   : cmax(MINB, 256 / TF));
     static constexpr int THREADS = TF * BATCH;
     static constexpr int CPP = F64 ? 1 : 2;                      // complex per 16-byte unit
     static constexpr int NPL = NC / CPP;                         // units per point in the CTA
-    static constexpr int UPP = 4 / CPP;                          // units per point in memory
+    static constexpr int PPP = 2 / CPP;                          // units per point per pair
     static constexpr int NPAIRS = 4 / NC;
     static constexpr int NST = plan_nst(LOGN, LOGE);
     static constexpr int SMEM_BYTES = (NST > 1 ? BATCH * NPL * N * 16 : 16);
@@ -187,6 +204,12 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
     KD_DI static int point_of(const SweepArgs& a, int line, int idx) {
         return AXIS == AXIS_X ? line * a.nx + idx : idx * a.nx + line;
     }
+    // spinor memory: two pair planes [pair][ny][nx][2 complex]; plane p of this CTA
+    KD_DI static long long unit_of(const SweepArgs& a, const Ctx& c, long long pt, int p) {
+        const int pair = NC == 4 ? p / Cf::PPP : c.pair;
+        const int u = p % Cf::PPP;
+        return ((long long)pair * a.nx * a.ny + pt) * Cf::PPP + u;
+    }
     KD_DI static int sm_addr(const Ctx& c, int p, int sw) {
         return AXIS == AXIS_X ? (c.bb * NPL + p) * N + sw : (p * N + sw) * BATCH + c.bb;
     }
@@ -201,11 +224,11 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 int idx = c.jt + m * TF + r * (N / R);
-                long long base = (long long)point_of(a, c.line, idx) * Cf::UPP + c.pair * NPL;
+                const long long pt = point_of(a, c.line, idx);
 #pragma unroll
                 for (int p = 0; p < NPL; ++p) {
                     U u;
-                    if (c.valid) u = g[base + p];
+                    if (c.valid) u = g[unit_of(a, c, pt, p)];
                     else u = U{};
                     Unit<T>::unpack(u, v + (m * R + r) * NC + p * CPP);
                 }
@@ -220,9 +243,9 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 int idx = c.jt + m * TF + r * (N / R);
-                long long base = (long long)point_of(a, c.line, idx) * Cf::UPP + c.pair * NPL;
+                const long long pt = point_of(a, c.line, idx);
 #pragma unroll
-                for (int p = 0; p < NPL; ++p) g[base + p] = Unit<T>::pack(v + (m * R + r) * NC + p * CPP);
+                for (int p = 0; p < NPL; ++p) g[unit_of(a, c, pt, p)] = Unit<T>::pack(v + (m * R + r) * NC + p * CPP);
             }
     }
 
@@ -239,10 +262,25 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
                 constexpr int STEP = N >> (LNS + LR);  // N / (Ns R)
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    C w = __ldg(tw + r * k * STEP);
-                    if (DIR > 0) w.y = -w.y;
+                    if constexpr (sizeof(T) == 4) {
+                        // FP32 twiddle as hi + lo pairs, applied by one FMA chain per
+                        // component: a single rounded twiddle has |w| != 1 by ~3e-8 and
+                        // the FFT would shrink or grow the norm coherently every step
+                        const float4 w4 = __ldg(reinterpret_cast<const float4*>(a.tw) + r * k * STEP);
+                        const float sh = DIR > 0 ? -w4.y : w4.y, sl = DIR > 0 ? -w4.w : w4.w;
 #pragma unroll
-                    for (int q = 0; q < NC; ++q) b[r * NC + q] = cmul(b[r * NC + q], w);
+                        for (int q = 0; q < NC; ++q) {
+                            const C x = b[r * NC + q];
+                            const float re = fmaf(x.x, w4.x, fmaf(-x.y, sh, fmaf(x.x, w4.z, -x.y * sl)));
+                            const float im = fmaf(x.x, sh, fmaf(x.y, w4.x, fmaf(x.x, sl, x.y * w4.z)));
+                            b[r * NC + q] = mk<C>(re, im);
+                        }
+                    } else {
+                        C w = __ldg(tw + r * k * STEP);
+                        if (DIR > 0) w.y = -w.y;
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) b[r * NC + q] = cmul(b[r * NC + q], w);
+                    }
                 }
             }
 #pragma unroll
@@ -298,11 +336,39 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
     }
 
     // --------------------------------------------------------- pointwise ops -------
+    // cos(theta) - 1 and sin(theta)/theta as Taylor series in theta^2 (theta < 1/4):
+    // truncation below 1e-13 (FP32 terms) and 1e-20 (FP64 terms), so the factor
+    // (1 + c1) + i s alpha.a stays unitary far below the rounding unit
+    KD_DI static void small_rotation(T th2, T* c1, T* sinc) {
+        if constexpr (sizeof(T) == 4) {
+            *c1 = th2 * (-0.5f + th2 * (1.0f / 24 + th2 * (-1.0f / 720 + th2 * (1.0f / 40320))));
+            *sinc = 1.0f + th2 * (-1.0f / 6 + th2 * (1.0f / 120 + th2 * (-1.0f / 5040 + th2 * (1.0f / 362880))));
+        } else {
+            *c1 = th2 * (-0.5 + th2 * (1.0 / 24 + th2 * (-1.0 / 720 + th2 * (1.0 / 40320 +
+                  th2 * (-1.0 / 3628800 + th2 * (1.0 / 479001600))))));
+            *sinc = 1.0 + th2 * (-1.0 / 6 + th2 * (1.0 / 120 + th2 * (-1.0 / 5040 + th2 * (1.0 / 362880 +
+                    th2 * (-1.0 / 39916800 + th2 * (1.0 / 6227020800.0))))));
+        }
+    }
+    KD_DI static T fexp(T x) {
+        if constexpr (sizeof(T) == 4) return __expf(x); else return exp(x);
+    }
+    KD_DI static void fsincos(T x, T* s, T* c) {
+        if constexpr (sizeof(T) == 4) __sincosf(x, s, c); else sincos(x, s, c);
+    }
+
     // potential factor exp(-i tau V/hbar), V = -m c^2 alpha.a, on registers in the op
-    // layout (element index j + r N/R_op is the x index of the row)
+    // layout (element index j + r N/R_op is the x index of the row).  The standing wave
+    // sum over d = +-1 of Eqs. (Equation_of_Gaussian_beam) is taken in product form:
+    //   a_y = -2 s(t) G cos(Theta),  a_x = 4 eps s(t) (y/w) G sin(Theta + zeta),
+    //   G = (w0/w) exp(-y^2/w^2),  Theta = -k x + zeta - x y^2/(x_R w^2),  zeta = atan(x/x_R),
+    // with s(t) = a0 f(t) sin(omega t + phase0) from the FP64 per-step table and the
+    // x-dependent parts from the FP64 per-x table.  FP32 uses the SFU exp/sincos on
+    // |Theta| <= pi + 1 (absolute error ~5e-7 of the field, no effect on unitarity).
     KD_DI static void op_potential(const SweepArgs& a, const Ctx& c, C* v) {
         if (a.kind == 0) return;
         constexpr int R = 1 << LR_OP;
+        using T4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
         const Clock ck = *a.clock;
         const StepScalars ss = a.steps[(ck.step - ck.base) + a.n_local];
         const double yrow = a.y_min + (double)c.line * a.dy + ss.Y;
@@ -310,34 +376,43 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
         const T y2 = y * y;
         const T st = (T)ss.s;
         const T kap = (T)a.kappa;
-        const T* xt = reinterpret_cast<const T*>(a.xtab);
-        const int nx = a.nx;
+        const T kap2 = kap * kap;
+        const T e4 = (T)a.eps4;
+        const T4* xt = reinterpret_cast<const T4*>(a.xtab);
 #pragma unroll
         for (int m = 0; m < E / R; ++m)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int x = c.jt + m * TF + r * (N / R);
-                T ax, ay;
+                const T4 t1 = xt[2 * x + 1];     // (1/w, cos zeta, sin zeta, cos k x)
+                T ax = T(0), ay;
                 if (a.kind == 1) {
-                    ax = T(0);
-                    ay = T(-2) * st * __ldg(xt + x);
+                    ay = T(-2) * st * t1.w;
                 } else {
-                    const T th0 = __ldg(xt + x), zeta = __ldg(xt + nx + x), cc = __ldg(xt + 2 * nx + x);
-                    const T gw = __ldg(xt + 3 * nx + x), iw2 = __ldg(xt + 4 * nx + x);
-                    const T G = gw * exp(-y2 * iw2);
-                    const T th = th0 - cc * y2;
-                    ay = T(-2) * st * G * cos(th);
-                    ax = T(0);
-                    if (a.longitudinal) {
-                        const T invw = __ldg(xt + 5 * nx + x);
-                        ax = (T)a.eps4 * st * (y * invw) * G * sin(th + zeta);
-                    }
+                    const T4 t0 = xt[2 * x];     // (Theta0, x/(x_R w^2), w0/w, 1/w^2)
+                    const T G = t0.z * fexp(-y2 * t0.w);
+                    T th = t0.x - t0.y * y2;
+                    if constexpr (sizeof(T) == 4) th -= 6.283185307f * rintf(th * 0.159154943f);
+                    T sn, cs;
+                    fsincos(th, &sn, &cs);
+                    const T sg = st * G;
+                    ay = T(-2) * sg * cs;
+                    if (a.longitudinal) ax = e4 * sg * (y * t1.x) * (sn * t1.y + cs * t1.z);
                 }
-                const T amag = sqrt(ax * ax + ay * ay);
-                const T th = kap * amag;
-                T sn, cs;
-                sincos_(th, &sn, &cs);
-                const T s = amag > T(0) ? sn / amag : kap;
+                const T a2 = ax * ax + ay * ay;
+                const T th2 = kap2 * a2;
+                T c1, s;   // cos(theta) - 1 and sin(theta)/|a|, theta = kappa |a|
+                if (th2 < T(0.0625)) {
+                    T sinc;
+                    small_rotation(th2, &c1, &sinc);
+                    s = kap * sinc;
+                } else {
+                    const T amag = sqrt(a2);
+                    T sh, ch;
+                    sincos_(T(0.5) * kap * amag, &sh, &ch);
+                    c1 = T(-2) * sh * sh;
+                    s = T(2) * sh * ch / amag;
+                }
                 C* e = v + (m * R + r) * NC;
 #pragma unroll
                 for (int q = 0; q < NC / 2; ++q) {
@@ -346,19 +421,26 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
                     const C u = e[2 * q], l = e[2 * q + 1];
                     const C q1 = mk<C>(s * sg * ay, s * ax);
                     const C q2 = mk<C>(-s * sg * ay, s * ax);
-                    e[2 * q] = cadd(mk<C>(cs * u.x, cs * u.y), cmul(q1, l));
-                    e[2 * q + 1] = cadd(mk<C>(cs * l.x, cs * l.y), cmul(q2, u));
+                    const C du = cadd(mk<C>(c1 * u.x, c1 * u.y), cmul(q1, l));
+                    const C dl = cadd(mk<C>(c1 * l.x, c1 * l.y), cmul(q2, u));
+                    e[2 * q] = cadd(u, du);
+                    e[2 * q + 1] = cadd(l, dl);
                 }
             }
     }
 
-    // kinetic factor [C - i S H0(pi)] e^{i phi_frame} / P on registers; element index is
-    // k_y, the line is k_x
+    // kinetic factor e^{i phi} [C - i S H0(pi)] / P on registers; element index is k_y,
+    // the line is k_x.  Stored as small numbers so that no constant next to 1 is rounded:
+    // per point a = (C - 1)/P and b = c S/P (chosen so that the factor built from the
+    // same rounded pi and m c as below is unitary to ~1e-11), per row f = e^{i phi} - 1
+    // (unit modulus of 1 + f to ~1e-12).  Applied as psi/P + a psi - i b (H0/c) psi, then
+    // times 1 + f; each result is a rounding around psi itself, which carries no bias.
     KD_DI static void op_kinetic(const SweepArgs& a, const Ctx& c, C* v) {
         constexpr int R = 1 << LR_OP;
         const C* kt = reinterpret_cast<const C*>(a.ktab);
         const T pix = __ldg(reinterpret_cast<const T*>(a.kxtab) + c.line);
         const T mc = (T)a.mc;
+        const T invP = T(1) / (T)((double)a.nx * (double)a.ny);   // exact: power of two
         using T4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
         const T4* kyt = reinterpret_cast<const T4*>(a.kytab);
 #pragma unroll
@@ -366,23 +448,23 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int ky = c.jt + m * TF + r * (N / R);
-                const C cs = __ldg(kt + (long long)ky * a.nx + c.line);
-                const T4 yv = kyt[ky];
-                const T Cp = cs.x, Sp = cs.y;
-                const T mcS = Sp * mc;
-                const C ph = mk<C>(yv.y, yv.z);
-                const C d1 = cmul(ph, mk<C>(Cp, -mcS));
-                const C d2 = cmul(ph, mk<C>(Cp, mcS));
+                const C ab = __ldg(kt + (long long)ky * a.nx + c.line);
+                const T4 yv = kyt[ky];                   // (pi_y, cos phi - 1, sin phi, 0)
                 C* e = v + (m * R + r) * NC;
 #pragma unroll
                 for (int q = 0; q < NC / 2; ++q) {
                     const int pr = NC == 4 ? q : c.pair;
-                    const T sg = pr == 0 ? T(1) : T(-1);
-                    const C o1 = cmul(ph, mk<C>(-Sp * sg * yv.x, -Sp * pix));
-                    const C o2 = cmul(ph, mk<C>(Sp * sg * yv.x, -Sp * pix));
+                    const T piy = pr == 0 ? yv.x : -yv.x;
                     const C u = e[2 * q], l = e[2 * q + 1];
-                    e[2 * q] = cadd(cmul(d1, u), cmul(o1, l));
-                    e[2 * q + 1] = cadd(cmul(d2, l), cmul(o2, u));
+                    // G = H0/c on the pair: (mc u + (pix - i piy) l, (pix + i piy) u - mc l)
+                    const C hu = mk<C>(mc * u.x + pix * l.x + piy * l.y, mc * u.y + pix * l.y - piy * l.x);
+                    const C hl = mk<C>(pix * u.x - piy * u.y - mc * l.x, pix * u.y + piy * u.x - mc * l.y);
+                    // u/P + a u - i b hu
+                    const C u1 = mk<C>(u.x * invP + (ab.x * u.x + ab.y * hu.y), u.y * invP + (ab.x * u.y - ab.y * hu.x));
+                    const C l1 = mk<C>(l.x * invP + (ab.x * l.x + ab.y * hl.y), l.y * invP + (ab.x * l.y - ab.y * hl.x));
+                    // times 1 + f (frame translation phase)
+                    e[2 * q] = mk<C>(u1.x + (yv.y * u1.x - yv.z * u1.y), u1.y + (yv.y * u1.y + yv.z * u1.x));
+                    e[2 * q + 1] = mk<C>(l1.x + (yv.y * l1.x - yv.z * l1.y), l1.y + (yv.y * l1.y + yv.z * l1.x));
                 }
             }
     }
@@ -396,8 +478,9 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
         const int tid = threadIdx.x;
         if (AXIS == AXIS_X) { c.bb = tid / TF; c.jt = tid % TF; }
         else { c.bb = tid % BATCH; c.jt = tid / BATCH; }
-        c.pair = NC == 2 ? (int)blockIdx.y : 0;
-        c.line = (int)blockIdx.x * BATCH + c.bb;
+        // the pair index varies fastest so both pairs of a line tile run together
+        c.pair = NC == 2 ? (int)(blockIdx.x % Cf::NPAIRS) : 0;
+        c.line = (int)(blockIdx.x / Cf::NPAIRS) * BATCH + c.bb;
         c.valid = c.line < (AXIS == AXIS_X ? a.ny : a.nx);
         c.sm = reinterpret_cast<U*>(smem_raw);
         C v[E * NC];
@@ -428,7 +511,7 @@ cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
         attr_done = true;
     }
     const int lines = AXIS == AXIS_X ? a.ny : a.nx;
-    dim3 grid((lines + Cf::BATCH - 1) / Cf::BATCH, Cf::NPAIRS);
+    dim3 grid(((lines + Cf::BATCH - 1) / Cf::BATCH) * Cf::NPAIRS);
     k<<<grid, Cf::THREADS, Cf::SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
