@@ -187,6 +187,34 @@ int kd_bench_sweep(kd_sim* sim, int32_t kind, int32_t reps);
  * node by node). */
 int kd_get_launch_count(kd_sim* sim, int64_t* launches);
 
+/* Allocation-free density read-out (no counterpart in the paper; the paper's
+ * Eqs. probability_density and y_integrated_probability_density define the values).
+ *
+ * For callers that cannot allocate device memory: code running while a stream is being
+ * captured into a CUDA graph (allocation calls are not permitted there), real-time loops
+ * that must never block on the allocator, and hosts that hand the library a fixed memory
+ * budget.  It needs no kd_sim and calls no cudaMalloc/cudaFree: its only scratch is a
+ * static device array of KD_NOALLOC_MAX_ROWS doubles (32 KiB) that every GPU which loads
+ * the library holds until the process exits.
+ *
+ *  psi            device pointer, [ny][nx][4] complex spinor in the layout above,
+ *                 complex128 (KD_FP64) or complex64 (KD_FP32); caller-owned
+ *  dx, dy         grid spacings
+ *  norm_out       device pointer to one double: sum |psi|^2 dx dy (may be NULL)
+ *  density_x_out  device pointer to nx doubles: Phi(x) = sum_y |psi|^2 dy (may be NULL)
+ *  cuda_stream    cudaStream_t the work is ordered on (NULL = legacy default stream)
+ * Returns KD_ERR_UNSUPPORTED_SIZE if ny > KD_NOALLOC_MAX_ROWS or nx > 4096, KD_ERR_ARG for
+ * null pointers, KD_ERR_CUDA on launch failure.  Asynchronous on the stream.
+ *
+ * The first call on each device looks up the scratch array's device address with that
+ * device current; make that first call before any stream capture.  All calls on a device
+ * share the one scratch array (each call overwrites every entry it reads, so nothing needs
+ * clearing): calls whose kernels can overlap on the GPU (different streams without
+ * ordering) race on it and must be serialised by the caller. */
+#define KD_NOALLOC_MAX_ROWS 4096
+int kd_density_noalloc(const void* psi, int32_t nx, int32_t ny, int32_t precision, double dx,
+                       double dy, double* norm_out, double* density_x_out, void* cuda_stream);
+
 /* Frees the simulation's device memory and CUDA graphs.  NULL is a no-op. */
 void kd_destroy(kd_sim* sim);
 

@@ -65,6 +65,11 @@ struct GraphKey {
 
 }  // namespace
 
+namespace kd {
+// Records a message for kd_last_error() from another translation unit.
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace kd
+
 struct kd_sim {
     kd_units u;
     kd_grid g;

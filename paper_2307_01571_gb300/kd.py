@@ -92,6 +92,8 @@ _SIGS = {
     "kd_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "kd_bench_sweep": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "kd_get_launch_count": (C.c_int, [_vp, _P(C.c_int64)]),
+    "kd_density_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                     C.c_double, _vp, _vp, _vp]),
     "kd_destroy": (None, [_vp]),
     "kd_last_error": (C.c_char_p, []),
     "kd_version": (C.c_int, []),
