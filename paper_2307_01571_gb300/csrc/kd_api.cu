@@ -182,7 +182,7 @@ __global__ void k_ktab(T* out, int nx, int ny, double dpx, double dpy, double sh
 // s(t) = a0 f(t) sin(omega t + phase0) and the co-moving box offset.
 __global__ void k_step_scalars(StepScalars* out, int64_t n, double t0, int64_t step0, double dt,
                                double a0, double omega, double phase0, double env_T,
-                               double box_vy) {
+                               double box_vy, double y_min) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > n) return;
     const double t = t0 + (double)(step0 + i) * dt;
@@ -194,8 +194,9 @@ __global__ void k_step_scalars(StepScalars* out, int64_t n, double t0, int64_t s
     StepScalars r;
     r.t = t;
     r.s = a0 * f * sin(omega * t + phase0);
-    r.Y = box_vy * t;
-    r.pad = 0.0;
+    r.ybase = y_min + box_vy * t;
+    r.s_f = (float)r.s;
+    r.ybase_f = (float)r.ybase;
     out[i] = r;
 }
 
@@ -447,47 +448,38 @@ int grid_blocks(size_t n, int threads) { return (int)((n + threads - 1) / thread
 
 template <typename T> int upload_tables_t(kd_sim* s) {
     const int nx = s->g.nx, ny = s->g.ny;
-    // twiddles exp(-2 pi i m / N) from FP64; FP32 entries are hi + lo pairs
-    // (c_hi, s_hi, c_lo, s_lo) so that the sweeps apply them to ~1e-15
+    // stage-major twiddle tables, built on the device in FP64 (<= 2N entries of 16 B)
     for (int ax = 0; ax < 2; ++ax) {
-        const int n = ax == 0 ? nx : ny;
-        const int stride = sizeof(T) == 4 ? 4 : 2;
-        std::vector<T> tw(stride * (size_t)n, (T)0);
-        for (int m = 0; m < n; ++m) {
-            const double a = 2.0 * kPi * m / n;
-            const double c = cos(a), sn = -sin(a);
-            tw[stride * m] = (T)c;
-            tw[stride * m + 1] = (T)sn;
-            if (stride == 4) {
-                tw[stride * m + 2] = (T)(c - (double)(T)c);
-                tw[stride * m + 3] = (T)(sn - (double)(T)sn);
-            }
-        }
-        KD_CUDA(cudaMemcpy(ax == 0 ? s->tw_x : s->tw_y, tw.data(), tw.size() * sizeof(T),
-                           cudaMemcpyHostToDevice));
+        int entries = 0;
+        const int logn = ax == 0 ? s->lx : s->ly;
+        void* dst = ax == 0 ? s->tw_x : s->tw_y;
+        KD_CUDA(sizeof(T) == 4 ? build_twiddles_f32(logn, dst, &entries, s->stream)
+                               : build_twiddles_f64(logn, dst, &entries, s->stream));
+        if (entries > 2 * (1 << logn)) return fail(KD_ERR_CUDA, "twiddle table overflow");
     }
     // per-x field table (Eqs. Equation_of_Gaussian_beam, Phase_of_Gaussian_beam and w(x)),
-    // 8 entries per column: Theta0 = (-k x + zeta) mod 2 pi, x/(x_R w^2), w0/w, 1/w^2, 1/w,
-    // cos zeta, sin zeta (zeta = atan(x/x_R)), cos k x (plane wave)
+    // two 4-vectors per column stored as [2][nx]: (Theta0 = (-k x + zeta) mod 2 pi,
+    // x/(x_R w^2), w0/w, 1/w^2) and (1/w, cos zeta, sin zeta, cos k x), zeta = atan(x/x_R)
     std::vector<T> xt(8 * (size_t)nx, (T)0);
     const double dx = (s->g.x_max - s->g.x_min) / nx;
     const double k = s->f.k_L;
     for (int i = 0; i < nx; ++i) {
         const double x = s->g.x_min + i * dx;
-        T* e = xt.data() + 8 * (size_t)i;
-        e[7] = (T)cos(k * x);
+        T* e0 = xt.data() + 4 * (size_t)i;          // first vector of column i
+        T* e1 = xt.data() + 4 * ((size_t)nx + i);   // second vector of column i
+        e1[3] = (T)cos(k * x);
         if (s->f.kind == KD_FIELD_GAUSS) {
             const double w0 = 1.0 / (k * s->f.epsilon);
             const double xR = k * w0 * w0 / 2.0;
             const double w = w0 * sqrt(1.0 + x * x / (xR * xR));
             const double zeta = atan(x / xR);
-            e[0] = (T)remainder(-k * x + zeta, 2.0 * kPi);
-            e[1] = (T)(x / (xR * w * w));
-            e[2] = (T)(w0 / w);
-            e[3] = (T)(1.0 / (w * w));
-            e[4] = (T)(1.0 / w);
-            e[5] = (T)cos(zeta);
-            e[6] = (T)sin(zeta);
+            e0[0] = (T)remainder(-k * x + zeta, 2.0 * kPi);
+            e0[1] = (T)(x / (xR * w * w));
+            e0[2] = (T)(w0 / w);
+            e0[3] = (T)(1.0 / (w * w));
+            e1[0] = (T)(1.0 / w);
+            e1[1] = (T)cos(zeta);
+            e1[2] = (T)sin(zeta);
         }
     }
     KD_CUDA(cudaMemcpy(s->xtab, xt.data(), xt.size() * sizeof(T), cudaMemcpyHostToDevice));
@@ -576,6 +568,12 @@ cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* 
     a.kxtab = s->kxtab;
     a.kytab = s->kytab;
     a.mc = s->u.m * s->u.c;
+    a.kappa_f = (float)a.kappa;
+    a.eps4_f = (float)a.eps4;
+    a.dy_f = (float)a.dy;
+    a.mc_f = (float)a.mc;
+    a.invP = 1.0 / ((double)s->g.nx * (double)s->g.ny);
+    a.invP_f = (float)a.invP;
     const int logn = axis == AXIS_X ? s->lx : s->ly;
     ++s->launches;
     return s->prec == KD_FP64 ? launch_sweep_f64(axis, shape, logn, a, s->stream)
@@ -879,8 +877,8 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
         return bail(fail(KD_ERR_CUDA, "stream create failed"));
     KD_ALLOC(s->psi, spinor_bytes(s));
     KD_ALLOC(s->work, spinor_bytes(s));
-    KD_ALLOC(s->tw_x, (size_t)grid->nx * 16);
-    KD_ALLOC(s->tw_y, (size_t)grid->ny * 16);
+    KD_ALLOC(s->tw_x, 2 * (size_t)grid->nx * 16);
+    KD_ALLOC(s->tw_y, 2 * (size_t)grid->ny * 16);
     KD_ALLOC(s->xtab, 8 * (size_t)grid->nx * s->tsize);
     KD_ALLOC(s->kxtab, (size_t)grid->nx * s->tsize);
     KD_ALLOC(s->kytab, 4 * (size_t)grid->ny * s->tsize);
@@ -1075,7 +1073,8 @@ int kd_step(kd_sim* s, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs
     }
     const double omega = s->u.c * s->f.k_L;
     k_step_scalars<<<grid_blocks((size_t)nsteps + 1, 256), 256, 0, s->stream>>>(
-        s->steps, nsteps, s->t0, s->step, dt, s->f.a0, omega, s->f.phase0, s->f.env_T, s->f.box_vy);
+        s->steps, nsteps, s->t0, s->step, dt, s->f.a0, omega, s->f.phase0, s->f.env_T, s->f.box_vy,
+        s->g.y_min);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
     k_set_clock<<<1, 1, 0, s->stream>>>(s->clock, 0);

@@ -23,10 +23,11 @@ enum SweepOp { OP_NONE = 0, OP_POTENTIAL = 1, OP_KINETIC = 2 };
 
 // Per-step scalars, FP64, written once per kd_step by a small kernel.
 struct StepScalars {
-    double t;   // time of the step boundary
-    double s;   // a0 f(t) sin(omega t + phase0): common factor of the standing wave
-    double Y;   // co-moving box offset box_vy t
-    double pad;
+    double t;      // time of the step boundary
+    double s;      // a0 f(t) sin(omega t + phase0): common factor of the standing wave
+    double ybase;  // y of row 0: y_min + box_vy t (co-moving box)
+    float s_f;     // the same two, rounded once for the FP32 sweeps
+    float ybase_f;
 };
 
 // Device clock: absolute step index of the state and the index at the start of the
@@ -39,8 +40,8 @@ struct Clock {
 struct SweepArgs {
     const void* in;
     void* out;
-    const void* tw;       // N twiddles exp(-2 pi i m / N): double2 (FP64) or float4
-                          // (c, s, d, 0) with |(c, s)| (1 + d) = 1 (FP32)
+    const void* tw;       // stage-major twiddle table (build_twiddles_*): double2 (FP64)
+                          // or float4 (c_hi, s_hi, c_lo, s_lo) (FP32)
     int nx, ny;
     int op;
     // potential (x sweep)
@@ -51,8 +52,12 @@ struct SweepArgs {
     double kappa;         // tau m c^2 / hbar for this sweep (tau = dt or dt/2)
     double eps4;          // 4 epsilon (longitudinal amplitude factor)
     double y_min, dy;
-    const void* xtab;     // [nx][8] per-x field table, precision of the sweep:
-                          // (Theta0, x/(x_R w^2), w0/w, 1/w^2, 1/w, cos zeta, sin zeta, cos k x)
+    // FP32 copies of the scalars, rounded once on the host, so that the FP32 sweeps do
+    // no FP64 arithmetic (the FP64 pipe is 1/64 of FP32 on GB300)
+    float kappa_f, eps4_f, dy_f, mc_f, invP_f;
+    double invP;          // 1 / (nx ny), exact
+    const void* xtab;     // [2][nx][4] per-x field table, precision of the sweep:
+                          // (Theta0, x/(x_R w^2), w0/w, 1/w^2) then (1/w, cos zeta, sin zeta, cos k x)
     // kinetic (y sweep)
     const void* ktab;     // [ny][nx] (C/P, c S/P) pairs
     const void* kxtab;    // [nx] pi_x
@@ -63,5 +68,9 @@ struct SweepArgs {
 // Launches one sweep; returns cudaSuccess or the launch error.  logn in [2, 12].
 cudaError_t launch_sweep_f32(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_sweep_f64(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
+// Fills the stage-major twiddle table of an N = 2^logn sweep (at most 2N entries of 16 B)
+// and returns the number of entries.
+cudaError_t build_twiddles_f32(int logn, void* out, int* entries, cudaStream_t s);
+cudaError_t build_twiddles_f64(int logn, void* out, int* entries, cudaStream_t s);
 
 }  // namespace kd

@@ -25,6 +25,25 @@
 
 #include "kd_internal.h"
 
+// Launch shape of the FP32 sweeps (compile-time; the defaults are the measured best on
+// GB300 for the 1024x512 grid): threads per row CTA, threads per column-tile CTA, the
+// minimum column-tile width, and the resident warps per SM the register budget targets.
+#ifndef KD_X_THREADS
+#define KD_X_THREADS 128
+#endif
+#ifndef KD_Y_THREADS
+#define KD_Y_THREADS 512
+#endif
+#ifndef KD_Y_MINB
+#define KD_Y_MINB 8
+#endif
+#ifndef KD_RESIDENT_WARPS_X
+#define KD_RESIDENT_WARPS_X 28
+#endif
+#ifndef KD_RESIDENT_WARPS_Y
+#define KD_RESIDENT_WARPS_Y 32
+#endif
+
 namespace kd {
 
 #define KD_DI __device__ __forceinline__
@@ -118,6 +137,32 @@ __host__ __device__ constexpr int plan_logns(int logn, int loge, int s) {  // lo
     for (int i = 0; i < s; ++i) a += plan_logr(logn, loge, i);
     return a;
 }
+// Twiddle table layout: stage-major, one segment per stage order (plan order, then
+// reversed order), stages in execution order, entries [r - 1][k] for r = 1..R-1 and
+// k = 0..Ns-1, value exp(-2 pi i r k / (Ns R)).  A warp's lanes have consecutive k, so
+// every twiddle load is contiguous (or a broadcast when Ns < 32).
+__host__ __device__ constexpr int stage_lns(int logn, int loge, bool rev, int S) {
+    return rev ? logn - plan_logns(logn, loge, plan_nst(logn, loge) - S) : plan_logns(logn, loge, S);
+}
+__host__ __device__ constexpr int stage_lr(int logn, int loge, bool rev, int S) {
+    return plan_logr(logn, loge, rev ? plan_nst(logn, loge) - 1 - S : S);
+}
+__host__ __device__ constexpr int stage_tw_entries(int logn, int loge, bool rev, int S) {
+    return stage_lns(logn, loge, rev, S) > 0
+               ? ((1 << stage_lr(logn, loge, rev, S)) - 1) << stage_lns(logn, loge, rev, S)
+               : 0;
+}
+__host__ __device__ constexpr int tw_offset(int logn, int loge, bool rev, int S) {
+    int off = 0;
+    if (rev)
+        for (int i = 0; i < plan_nst(logn, loge); ++i) off += stage_tw_entries(logn, loge, false, i);
+    for (int i = 0; i < S; ++i) off += stage_tw_entries(logn, loge, rev, i);
+    return off;
+}
+__host__ __device__ constexpr int tw_total(int logn, int loge) {
+    return tw_offset(logn, loge, true, plan_nst(logn, loge));
+}
+
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
@@ -132,20 +177,27 @@ template <typename T, int LOGN, int AXIS> struct Cfg {
     static constexpr int LOGE = LOGN < LOGRMAX ? LOGN : LOGRMAX;
     static constexpr int E = 1 << LOGE;                          // elements per thread
     static constexpr int TF = N / E;                             // threads per line
-    // lines per CTA: rows are batched up to 128 threads; column tiles take 256 threads
-    // and at least 4 (FP32) or 2 (FP64) columns, i.e. >= 64 contiguous bytes per tile
-    // row, within 512 threads
-    static constexpr int MINB = F64 ? 2 : 4;
-    static constexpr int BATCH = AXIS == AXIS_X ? cmax(1, 128 / TF)
+    // lines per CTA: rows are batched up to KD_X_THREADS threads; column tiles take
+    // KD_Y_THREADS threads and at least KD_Y_MINB (FP32) or 2 (FP64) columns, i.e.
+    // >= 64-128 contiguous bytes per tile row, within 512 threads
+    static constexpr int MINB = F64 ? 2 : KD_Y_MINB;
+    static constexpr int BATCH = AXIS == AXIS_X ? cmax(1, (F64 ? 128 : KD_X_THREADS) / TF)
                                                 : (TF * MINB > 512 ? cmax(1, 512 / TF)
-                                                                   : cmax(MINB, 256 / TF));
+                                                                   : cmax(MINB, (F64 ? 256 : KD_Y_THREADS) / TF));
     static constexpr int THREADS = TF * BATCH;
     static constexpr int CPP = F64 ? 1 : 2;                      // complex per 16-byte unit
     static constexpr int NPL = NC / CPP;                         // units per point in the CTA
     static constexpr int PPP = 2 / CPP;                          // units per point per pair
     static constexpr int NPAIRS = 4 / NC;
     static constexpr int NST = plan_nst(LOGN, LOGE);
-    static constexpr int SMEM_BYTES = (NST > 1 ? BATCH * NPL * N * 16 : 16);
+    static constexpr int BUF_UNITS = BATCH * NPL * N;            // one exchange buffer
+    // resident CTAs per SM the FP32 sweeps are built for (KD_RESIDENT_WARPS warps, so the
+    // 1024x512 grid's lines fit in one wave); FP64 sweeps keep their full register budget
+    static constexpr int MINBLK =
+        F64 ? 1 : cmax(1, (AXIS == AXIS_X ? KD_RESIDENT_WARPS_X : KD_RESIDENT_WARPS_Y) * 32 / THREADS);
+    // two exchange buffers (one barrier per exchange) only when they keep that occupancy
+    static constexpr bool DB = 2 * BUF_UNITS * 16 * MINBLK <= 200 * 1024;
+    static constexpr int SMEM_BYTES = NST > 1 ? (DB ? 2 : 1) * BUF_UNITS * 16 : 16;
     // lanes of one 8-lane (128-byte) shared-memory wavefront cover 2^LOGG consecutive
     // butterflies
     static constexpr int LOGG =
@@ -154,8 +206,10 @@ template <typename T, int LOGN, int AXIS> struct Cfg {
 
 // XOR swizzle of element index i for the exchange after a stage with Ns = 2^la and
 // radix 2^lb: spreads the 2^g butterflies of a wavefront over distinct 16-byte bank
-// groups for the strided write and keeps the contiguous read conflict-free.
-template <int LA, int LB, int G> KD_DI int swz(int i) {
+// groups for the strided write and keeps the contiguous read conflict-free.  The map is
+// linear over GF(2) (swz(a ^ b) = swz(a) ^ swz(b)), which the exchange uses to reduce
+// every access to one XOR of a per-thread base with a compile-time constant.
+template <int LA, int LB, int G> __host__ __device__ constexpr int swz(int i) {
     if constexpr (LA >= G) {
         return i;
     } else {
@@ -163,6 +217,11 @@ template <int LA, int LB, int G> KD_DI int swz(int i) {
         constexpr int W = cmin(LB, G - LA);
         return i ^ (((i >> SH) & ((1 << W) - 1)) << LA);
     }
+}
+// Stockham output index of butterfly j before adding r Ns: (j / Ns) Ns R + j mod Ns
+// (also GF(2)-linear in j)
+template <int LA, int LB> __host__ __device__ constexpr int expand(int j) {
+    return ((j >> LA) << (LA + LB)) | (j & ((1 << LA) - 1));
 }
 
 // ------------------------------------------------------- register <-> 16 B --------
@@ -210,9 +269,6 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
         const int u = p % Cf::PPP;
         return ((long long)pair * a.nx * a.ny + pt) * Cf::PPP + u;
     }
-    KD_DI static int sm_addr(const Ctx& c, int p, int sw) {
-        return AXIS == AXIS_X ? (c.bb * NPL + p) * N + sw : (p * N + sw) * BATCH + c.bb;
-    }
 
     // registers hold slots e = m*R + r for butterfly j = jt + m*TF, element index
     // j + r*N/R (the input layout of a stage with radix R = 2^LR)
@@ -228,7 +284,9 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
 #pragma unroll
                 for (int p = 0; p < NPL; ++p) {
                     U u;
-                    if (c.valid) u = g[unit_of(a, c, pt, p)];
+                    // the spinor streams through L2 only (.cg), so that the small,
+                    // reused twiddle and field tables stay resident in L1
+                    if (c.valid) u = __ldcg(g + unit_of(a, c, pt, p));
                     else u = U{};
                     Unit<T>::unpack(u, v + (m * R + r) * NC + p * CPP);
                 }
@@ -245,28 +303,29 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
                 int idx = c.jt + m * TF + r * (N / R);
                 const long long pt = point_of(a, c.line, idx);
 #pragma unroll
-                for (int p = 0; p < NPL; ++p) g[unit_of(a, c, pt, p)] = Unit<T>::pack(v + (m * R + r) * NC + p * CPP);
+                for (int p = 0; p < NPL; ++p) __stcg(g + unit_of(a, c, pt, p), Unit<T>::pack(v + (m * R + r) * NC + p * CPP));
             }
     }
 
     // one Stockham stage: twiddle (Ns > 1) and radix-R butterflies on registers
-    template <int DIR, int LR, int LNS> KD_DI static void stage(const SweepArgs& a, const Ctx& c, C* v) {
+    // one Stockham stage: twiddle (Ns > 1) and radix-R butterflies on registers; the
+    // stage's twiddles start at entry TWOFF of the stage-major table
+    template <int DIR, int LR, int LNS, int TWOFF> KD_DI static void stage(const SweepArgs& a, const Ctx& c, C* v) {
         constexpr int R = 1 << LR;
-        const C* tw = reinterpret_cast<const C*>(a.tw);
+        constexpr int NS = 1 << LNS;
 #pragma unroll
         for (int m = 0; m < E / R; ++m) {
             C* b = v + m * R * NC;
             if constexpr (LNS > 0) {
-                int j = c.jt + m * TF;
-                int k = j & ((1 << LNS) - 1);
-                constexpr int STEP = N >> (LNS + LR);  // N / (Ns R)
+                const int k = (c.jt + m * TF) & (NS - 1);
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
+                    const int idx = TWOFF + (r - 1) * NS + k;
                     if constexpr (sizeof(T) == 4) {
                         // FP32 twiddle as hi + lo pairs, applied by one FMA chain per
                         // component: a single rounded twiddle has |w| != 1 by ~3e-8 and
                         // the FFT would shrink or grow the norm coherently every step
-                        const float4 w4 = __ldg(reinterpret_cast<const float4*>(a.tw) + r * k * STEP);
+                        const float4 w4 = __ldg(reinterpret_cast<const float4*>(a.tw) + idx);
                         const float sh = DIR > 0 ? -w4.y : w4.y, sl = DIR > 0 ? -w4.w : w4.w;
 #pragma unroll
                         for (int q = 0; q < NC; ++q) {
@@ -276,7 +335,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
                             b[r * NC + q] = mk<C>(re, im);
                         }
                     } else {
-                        C w = __ldg(tw + r * k * STEP);
+                        C w = __ldg(reinterpret_cast<const C*>(a.tw) + idx);
                         if (DIR > 0) w.y = -w.y;
 #pragma unroll
                         for (int q = 0; q < NC; ++q) b[r * NC + q] = cmul(b[r * NC + q], w);
@@ -288,49 +347,58 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
         }
     }
 
-    // shared-memory exchange from the output layout of stage (LA = log Ns, LB = log R)
-    // to the input layout of a stage with radix 2^LRN
-    template <int LA, int LB, int LRN> KD_DI static void exchange(const Ctx& c, C* v) {
+    // shared-memory unit of (plane p, swizzled index sw) within a buffer:
+    //   x axis: bb NPL N + p N + sw = (bb NPL N ^ sw) + p N
+    //   y axis: (p N + sw) BATCH + bb = ((sw << log BATCH) ^ bb) + p N BATCH
+    static constexpr int LOGB = clog2(BATCH);
+    static constexpr int PSTRIDE = AXIS == AXIS_X ? N : N * BATCH;
+    KD_DI static int fold(const Ctx& c) { return AXIS == AXIS_X ? c.bb * NPL * N : c.bb; }
+    __host__ __device__ static constexpr int lin(int sw) { return AXIS == AXIS_X ? sw : sw << LOGB; }
+
+    // shared-memory exchange XI (0, 1, ... in kernel order) from the output layout of a
+    // stage (LA = log Ns, LB = log R) to the input layout of a stage with radix 2^LRN.
+    // Consecutive exchanges alternate between two buffers when they fit (one barrier).
+    template <int LA, int LB, int LRN, int XI> KD_DI static void exchange(const Ctx& c, C* v) {
         constexpr int R = 1 << LB;
         constexpr int RN = 1 << LRN;
         constexpr int G = Cf::LOGG;
+        constexpr int BUF = Cf::DB ? (XI & 1) * Cf::BUF_UNITS : 0;
+        U* sm = c.sm + BUF;
+        // per-thread bases; j = jt + m TF = jt ^ (m TF) and both maps are XOR-linear
+        const int wb = fold(c) ^ lin(swz<LA, LB, G>(expand<LA, LB>(c.jt)));
+        const int rb = fold(c) ^ lin(swz<LA, LB, G>(c.jt));
 #pragma unroll
-        for (int m = 0; m < E / R; ++m) {
-            int j = c.jt + m * TF;
-            int hi = ((j >> LA) << (LA + LB)) | (j & ((1 << LA) - 1));
+        for (int m = 0; m < E / R; ++m)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                int sw = swz<LA, LB, G>(hi | (r << LA));
+                const int k = lin(swz<LA, LB, G>(expand<LA, LB>(m * TF)) ^ (r << LA));
 #pragma unroll
-                for (int p = 0; p < NPL; ++p) c.sm[sm_addr(c, p, sw)] = Unit<T>::pack(v + (m * R + r) * NC + p * CPP);
+                for (int p = 0; p < NPL; ++p) sm[(wb ^ k) + p * PSTRIDE] = Unit<T>::pack(v + (m * R + r) * NC + p * CPP);
             }
-        }
         __syncthreads();
 #pragma unroll
-        for (int m = 0; m < E / RN; ++m) {
-            int j = c.jt + m * TF;
+        for (int m = 0; m < E / RN; ++m)
 #pragma unroll
             for (int r = 0; r < RN; ++r) {
-                int sw = swz<LA, LB, G>(j | (r << (LOGN - LRN)));
+                const int k = lin(swz<LA, LB, G>((m * TF) | (r << (LOGN - LRN))));
 #pragma unroll
-                for (int p = 0; p < NPL; ++p) Unit<T>::unpack(c.sm[sm_addr(c, p, sw)], v + (m * RN + r) * NC + p * CPP);
+                for (int p = 0; p < NPL; ++p) Unit<T>::unpack(sm[(rb ^ k) + p * PSTRIDE], v + (m * RN + r) * NC + p * CPP);
             }
-        }
-        __syncthreads();
+        if constexpr (!Cf::DB) __syncthreads();
     }
 
     // FFT with stages in plan order (REV = false) or reversed plan order (REV = true)
-    template <int DIR, bool REV, int S> KD_DI static void fft(const SweepArgs& a, const Ctx& c, C* v) {
+    template <int DIR, bool REV, int XB, int S> KD_DI static void fft(const SweepArgs& a, const Ctx& c, C* v) {
         if constexpr (S < NST) {
             constexpr int PS = REV ? NST - 1 - S : S;              // plan index of this stage
             constexpr int LR = plan_logr(LOGN, Cf::LOGE, PS);
             constexpr int LNS = REV ? LOGN - plan_logns(LOGN, Cf::LOGE, PS + 1)
                                     : plan_logns(LOGN, Cf::LOGE, PS);
-            stage<DIR, LR, LNS>(a, c, v);
+            stage<DIR, LR, LNS, tw_offset(LOGN, Cf::LOGE, REV, S)>(a, c, v);
             if constexpr (S + 1 < NST) {
                 constexpr int PN = REV ? NST - 2 - S : S + 1;
-                exchange<LNS, LR, plan_logr(LOGN, Cf::LOGE, PN)>(c, v);
-                fft<DIR, REV, S + 1>(a, c, v);
+                exchange<LNS, LR, plan_logr(LOGN, Cf::LOGE, PN), XB + S>(c, v);
+                fft<DIR, REV, XB, S + 1>(a, c, v);
             }
         }
     }
@@ -370,26 +438,34 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
         constexpr int R = 1 << LR_OP;
         using T4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
         const Clock ck = *a.clock;
-        const StepScalars ss = a.steps[(ck.step - ck.base) + a.n_local];
-        const double yrow = a.y_min + (double)c.line * a.dy + ss.Y;
-        const T y = (T)yrow;
+        const StepScalars* ssp = a.steps + ((ck.step - ck.base) + a.n_local);
+        T y, st, kap, e4;
+        if constexpr (sizeof(T) == 4) {
+            y = ssp->ybase_f + (float)c.line * a.dy_f;
+            st = ssp->s_f;
+            kap = a.kappa_f;
+            e4 = a.eps4_f;
+        } else {
+            y = ssp->ybase + (double)c.line * a.dy;
+            st = ssp->s;
+            kap = a.kappa;
+            e4 = a.eps4;
+        }
         const T y2 = y * y;
-        const T st = (T)ss.s;
-        const T kap = (T)a.kappa;
         const T kap2 = kap * kap;
-        const T e4 = (T)a.eps4;
-        const T4* xt = reinterpret_cast<const T4*>(a.xtab);
+        const T4* xt = reinterpret_cast<const T4*>(a.xtab);   // [2][nx] vectors
+        const int nx = a.nx;
 #pragma unroll
         for (int m = 0; m < E / R; ++m)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int x = c.jt + m * TF + r * (N / R);
-                const T4 t1 = xt[2 * x + 1];     // (1/w, cos zeta, sin zeta, cos k x)
+                const T4 t1 = xt[nx + x];        // (1/w, cos zeta, sin zeta, cos k x)
                 T ax = T(0), ay;
                 if (a.kind == 1) {
                     ay = T(-2) * st * t1.w;
                 } else {
-                    const T4 t0 = xt[2 * x];     // (Theta0, x/(x_R w^2), w0/w, 1/w^2)
+                    const T4 t0 = xt[x];         // (Theta0, x/(x_R w^2), w0/w, 1/w^2)
                     const T G = t0.z * fexp(-y2 * t0.w);
                     T th = t0.x - t0.y * y2;
                     if constexpr (sizeof(T) == 4) th -= 6.283185307f * rintf(th * 0.159154943f);
@@ -439,8 +515,9 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
         constexpr int R = 1 << LR_OP;
         const C* kt = reinterpret_cast<const C*>(a.ktab);
         const T pix = __ldg(reinterpret_cast<const T*>(a.kxtab) + c.line);
-        const T mc = (T)a.mc;
-        const T invP = T(1) / (T)((double)a.nx * (double)a.ny);   // exact: power of two
+        T mc, invP;   // invP = 1/P is exact (power of two)
+        if constexpr (sizeof(T) == 4) { mc = a.mc_f; invP = a.invP_f; }
+        else { mc = a.mc; invP = a.invP; }
         using T4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
         const T4* kyt = reinterpret_cast<const T4*>(a.kytab);
 #pragma unroll
@@ -448,7 +525,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int ky = c.jt + m * TF + r * (N / R);
-                const C ab = __ldg(kt + (long long)ky * a.nx + c.line);
+                const C ab = __ldcg(kt + (long long)ky * a.nx + c.line);
                 const T4 yv = kyt[ky];                   // (pi_y, cos phi - 1, sin phi, 0)
                 C* e = v + (m * R + r) * NC;
 #pragma unroll
@@ -485,16 +562,16 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
         c.sm = reinterpret_cast<U*>(smem_raw);
         C v[E * NC];
         load<LR_LOAD>(a, c, v);
-        if constexpr (HAS1) fft<DIR1, false, 0>(a, c, v);
+        if constexpr (HAS1) fft<DIR1, false, 0, 0>(a, c, v);
         if (AXIS == AXIS_X && a.op == OP_POTENTIAL) op_potential(a, c, v);
         if (AXIS == AXIS_Y && a.op == OP_KINETIC) op_kinetic(a, c, v);
-        if constexpr (HAS2) fft<DIR2, true, 0>(a, c, v);
+        if constexpr (HAS2) fft<DIR2, true, HAS1 ? NST - 1 : 0, 0>(a, c, v);
         store<LR_STORE>(a, c, v);
     }
 };
 
 template <typename T, int LOGN, int AXIS, int SHAPE>
-__global__ void __launch_bounds__(Cfg<T, LOGN, AXIS>::THREADS)
+__global__ void __launch_bounds__(Cfg<T, LOGN, AXIS>::THREADS, Cfg<T, LOGN, AXIS>::MINBLK)
 sweep_kernel(const SweepArgs a) {
     Sweep<T, LOGN, AXIS, SHAPE>::run(a);
 }
@@ -514,6 +591,66 @@ cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
     dim3 grid(((lines + Cf::BATCH - 1) / Cf::BATCH) * Cf::NPAIRS);
     k<<<grid, Cf::THREADS, Cf::SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
+}
+
+// Fills the stage-major twiddle table of an N = 2^LOGN sweep in FP64 (sincospi):
+// FP32 entries are float4 (c_hi, s_hi, c_lo, s_lo), FP64 entries double2 (c, s).
+template <typename T, int LOGN>
+__global__ void twiddle_kernel(void* out) {
+    constexpr int LOGE = Cfg<T, LOGN, AXIS_X>::LOGE;
+    constexpr int NST = plan_nst(LOGN, LOGE);
+    const int total = tw_total(LOGN, LOGE);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        // find the (order, stage) segment holding entry e and the index within it
+        int idx = e, lns = 0, lr = 0;
+        bool found = false;
+        for (int o = 0; o < 2 && !found; ++o)
+            for (int S = 0; S < NST && !found; ++S) {
+                const int n = stage_tw_entries(LOGN, LOGE, o == 1, S);
+                if (idx < n) {
+                    lns = stage_lns(LOGN, LOGE, o == 1, S);
+                    lr = stage_lr(LOGN, LOGE, o == 1, S);
+                    found = true;
+                } else {
+                    idx -= n;
+                }
+            }
+        const int ns = 1 << lns;
+        const int r = idx / ns + 1, k = idx % ns;
+        double sn, cs;
+        sincospi(2.0 * (double)(r * k) / (double)(ns << lr), &sn, &cs);
+        sn = -sn;
+        if constexpr (sizeof(T) == 4) {
+            const float ch = (float)cs, sh = (float)sn;
+            reinterpret_cast<float4*>(out)[e] = make_float4(ch, sh, (float)(cs - (double)ch), (float)(sn - (double)sh));
+        } else {
+            reinterpret_cast<double2*>(out)[e] = make_double2(cs, sn);
+        }
+    }
+}
+
+template <typename T, int LOGN> cudaError_t build_tw(void* out, int* entries, cudaStream_t s) {
+    constexpr int LOGE = Cfg<T, LOGN, AXIS_X>::LOGE;
+    *entries = tw_total(LOGN, LOGE);
+    if (*entries > 0) twiddle_kernel<T, LOGN><<<(*entries + 255) / 256, 256, 0, s>>>(out);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t build_twiddles(int logn, void* out, int* entries, cudaStream_t s) {
+    switch (logn) {
+        case 2: return build_tw<T, 2>(out, entries, s);
+        case 3: return build_tw<T, 3>(out, entries, s);
+        case 4: return build_tw<T, 4>(out, entries, s);
+        case 5: return build_tw<T, 5>(out, entries, s);
+        case 6: return build_tw<T, 6>(out, entries, s);
+        case 7: return build_tw<T, 7>(out, entries, s);
+        case 8: return build_tw<T, 8>(out, entries, s);
+        case 9: return build_tw<T, 9>(out, entries, s);
+        case 10: return build_tw<T, 10>(out, entries, s);
+        case 11: return build_tw<T, 11>(out, entries, s);
+        case 12: return build_tw<T, 12>(out, entries, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T, int AXIS, int SHAPE>
