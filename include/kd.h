@@ -180,7 +180,8 @@ int kd_set_state(kd_sim* sim, const void* buf, size_t size);
  * x-FFT; the row pass of one Strang step, Sec. II.D), kind 1 = y sweep (forward y-FFT,
  * kinetic step, inverse y-FFT; the column pass).  Uses the tables and time of the last
  * kd_step call (KD_ERR_ARG before any kd_step).  The state is left in an unspecified
- * mixed representation: call it on a scratch simulation, or restore a checkpoint after. */
+ * mixed representation: call it on a scratch simulation, or restore a checkpoint after.
+ * The launches of one (kind, reps) pair are captured once into a CUDA graph and replayed. */
 int kd_bench_sweep(kd_sim* sim, int32_t kind, int32_t reps);
 
 /* Number of kernel launches this simulation has enqueued so far (graph replays counted

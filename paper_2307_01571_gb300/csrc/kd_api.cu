@@ -1192,12 +1192,42 @@ int kd_bench_sweep(kd_sim* s, int32_t kind, int32_t reps) {
     if (rc) return rc;
     if ((kind != 0 && kind != 1) || reps < 0) return fail(KD_ERR_ARG, "kind must be 0 or 1, reps >= 0");
     if (s->ktab_dt == 0.0 || !s->steps) return fail(KD_ERR_ARG, "call kd_step once before kd_bench_sweep");
-    k_set_clock<<<1, 1, 0, s->stream>>>(s->clock, 0);
-    KD_CUDA(cudaGetLastError());
-    for (int32_t i = 0; i < reps; ++i) {
-        if (kind == 0) KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F1F2, OP_POTENTIAL, s->psi, s->psi, 0, s->ktab_dt));
-        else KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F1F2, OP_KINETIC, s->psi, s->psi, 0, 0.0));
+    // the launches are captured once into a graph (per kind and count) and replayed, so
+    // that the GPU runs them back to back without host launch overhead
+    GraphKey key{-1 - kind, reps, 0};
+    auto it = s->graphs.find(key);
+    if (it == s->graphs.end()) {
+        cudaStream_t user = s->stream;
+        s->stream = s->cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            s->stream = user;
+            return fail(KD_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+        }
+        const int64_t before = s->launches;
+        cudaError_t el = cudaSuccess;
+        k_set_clock<<<1, 1, 0, s->stream>>>(s->clock, 0);
+        ++s->launches;
+        for (int32_t i = 0; i < reps && el == cudaSuccess; ++i)
+            el = kind == 0 ? sweep(s, AXIS_X, SHAPE_F1F2, OP_POTENTIAL, s->psi, s->psi, 0, s->ktab_dt)
+                           : sweep(s, AXIS_Y, SHAPE_F1F2, OP_KINETIC, s->psi, s->psi, 0, 0.0);
+        const int64_t nodes = s->launches - before;
+        s->launches = before;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(s->stream, &graph);
+        s->stream = user;
+        if (el != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(KD_ERR_CUDA, "bench capture: %s", cudaGetErrorString(el != cudaSuccess ? el : e));
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(KD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        it = s->graphs.emplace(key, std::make_pair(exec, nodes)).first;
     }
+    KD_CUDA(cudaGraphLaunch(it->second.first, s->stream));
+    s->launches += it->second.second;
     return KD_OK;
 }
 
