@@ -229,7 +229,8 @@ def main():
         sweep_ms = {}
         for kind, name in ((0, "x_sweep"), (1, "y_sweep")):
             reps = 200
-            sim.bench_sweep(kind, 5)
+            sim.bench_sweep(kind, reps)      # captures the replay graph (untimed)
+            torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             sim.bench_sweep(kind, reps)

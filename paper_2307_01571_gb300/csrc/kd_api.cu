@@ -215,12 +215,18 @@ __global__ void k_rowsum(const T* psi, int nx, int ny, double* rowsum) {
     __shared__ double red[256];
     const int row = blockIdx.x;
     const size_t P = (size_t)nx * ny;
+    // squares summed in groups of 8 in the spinor's precision, groups in FP64: keeps the
+    // FP32 sweeps' reduction off the slow FP64 pipe while the sum stays accurate to ~1e-9
     double acc = 0.0;
+    T part = T(0);
+    int cnt = 0;
     for (int i = threadIdx.x; i < nx * 8; i += blockDim.x) {
         const int pair = i / (nx * 4), k = i % (nx * 4);
-        const double v = (double)psi[(pair * P + (size_t)row * nx) * 4 + k];
-        acc += v * v;
+        const T v = psi[(pair * P + (size_t)row * nx) * 4 + k];
+        part += v * v;
+        if (++cnt == 8) { acc += (double)part; part = T(0); cnt = 0; }
     }
+    acc += (double)part;
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -355,10 +361,58 @@ __global__ void k_momentum_density(const T* phi, int nx, int ny, double dpx, dou
     out[(size_t)i * 3 + 2] = cpm[1] * cellw;
 }
 
-// One observation record from the row sums and the momentum density: window sums over
-// fixed index ranges in a fixed order (bitwise reproducible), status bits for the
+// Momentum-space cell values (|phi|^2, |c+|^2, |c-|^2) dx dy / P of the two observation
+// windows (row-major within each window) and the target cell, from phi = DFT psi in the
+// internal layout; FP64, one thread per cell.  out[cell][3].
+template <typename T>
+__global__ void k_obs_cells(const T* phi, int nx, int ny, double dpx, double dpy, double shx,
+                            double shy, double c, double mc2, int basis, double cellw, ObsWin w,
+                            double* out) {
+    const int n0 = (w.ihi[0] - w.ilo[0] + 1) * (w.jhi[0] - w.jlo[0] + 1);
+    const int n1 = (w.ihi[1] - w.ilo[1] + 1) * (w.jhi[1] - w.jlo[1] + 1);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > n0 + n1) return;
+    int i, j;
+    if (e < n0) {
+        const int wx = w.ihi[0] - w.ilo[0] + 1;
+        i = w.ilo[0] + e % wx; j = w.jlo[0] + e / wx;
+    } else if (e < n0 + n1) {
+        const int wx = w.ihi[1] - w.ilo[1] + 1;
+        i = w.ilo[1] + (e - n0) % wx; j = w.jlo[1] + (e - n0) / wx;
+    } else {
+        i = w.it; j = w.jt;
+    }
+    const int kx = (i + nx) % nx, ky = (j + ny) % ny;
+    const size_t pt = (size_t)ky * nx + kx;
+    const double pix = dpx * (kx < nx / 2 ? kx : kx - nx) + shx;
+    const double piy = dpy * (ky < ny / 2 ? ky : ky - ny) + shy;
+    double2 f[4];
+    for (int s = 0; s < 4; ++s) {
+        const size_t o = slot_off((size_t)nx * ny, pt, s);
+        f[perm_to_dirac(s)] = make_double2((double)phi[o], (double)phi[o + 1]);
+    }
+    double p2 = 0.0;
+    for (int d = 0; d < 4; ++d) p2 += f[d].x * f[d].x + f[d].y * f[d].y;
+    double cpm[2];
+    for (int si = 0; si < 2; ++si) {
+        double2 u[4];
+        bispinor(c, mc2, pix, piy, si == 0 ? 1 : -1, basis, u);
+        double re = 0.0, im = 0.0;
+        for (int d = 0; d < 4; ++d) {
+            re += u[d].x * f[d].x + u[d].y * f[d].y;
+            im += u[d].x * f[d].y - u[d].y * f[d].x;
+        }
+        cpm[si] = re * re + im * im;
+    }
+    out[(size_t)e * 3 + 0] = p2 * cellw;
+    out[(size_t)e * 3 + 1] = cpm[0] * cellw;
+    out[(size_t)e * 3 + 2] = cpm[1] * cellw;
+}
+
+// One observation record from the row sums and the window cells (k_obs_cells): window
+// sums in a fixed order (bitwise reproducible), status bits for the
 // watchdog (1: non-finite norm, 2: drift beyond tol relative to scalar[1]).
-__global__ void k_obs_reduce(const double* rowsum, const double* md, int nx, int ny, double cell,
+__global__ void k_obs_reduce(const double* rowsum, const double* cells, int nx, int ny, double cell,
                              ObsWin w, const StepScalars* steps, const Clock* clock, int n_local,
                              double t_fixed, int64_t obs_every, int64_t cap, kd_obs* out,
                              const double* scalar, double tol, int* status) {
@@ -390,13 +444,14 @@ __global__ void k_obs_reduce(const double* rowsum, const double* md, int nx, int
     for (int i = tid; i < ny; i += blockDim.x) acc += rowsum[i];
     const double norm = tree(acc) * cell;
     double sums[2][3], mx[3] = {0, 0, 0};
+    const int n0 = (w.ihi[0] - w.ilo[0] + 1) * (w.jhi[0] - w.jlo[0] + 1);
+    const int n1 = (w.ihi[1] - w.ilo[1] + 1) * (w.jhi[1] - w.jlo[1] + 1);
     for (int wi = 0; wi < 2; ++wi) {
-        const int wx = w.ihi[wi] - w.ilo[wi] + 1, wy = w.jhi[wi] - w.jlo[wi] + 1;
+        const int nc = wi == 0 ? n0 : n1;
+        const double* base = cells + (wi == 0 ? 0 : (size_t)n0 * 3);
         double a[3] = {0, 0, 0}, m[3] = {0, 0, 0};
-        for (int q = tid; q < wx * wy; q += blockDim.x) {
-            const int i = w.ilo[wi] + q % wx, j = w.jlo[wi] + q / wx;
-            const int kx = (i + nx) % nx, ky = (j + ny) % ny;
-            const double* o = md + ((size_t)ky * nx + kx) * 3;
+        for (int q = tid; q < nc; q += blockDim.x) {
+            const double* o = base + (size_t)q * 3;
             for (int k = 0; k < 3; ++k) { a[k] += o[k]; m[k] = fmax(m[k], o[k]); }
         }
         for (int k = 0; k < 3; ++k) sums[wi][k] = tree(a[k]);
@@ -411,8 +466,7 @@ __global__ void k_obs_reduce(const double* rowsum, const double* md, int nx, int
             slot = sidx / obs_every - 1;
             t = steps[sidx].t;
         }
-        const int kx = (w.it + nx) % nx, ky = (w.jt + ny) % ny;
-        const double* o = md + ((size_t)ky * nx + kx) * 3;
+        const double* o = cells + (size_t)(n0 + n1) * 3;
         kd_obs r;
         r.t = t;
         r.norm = norm;
@@ -653,16 +707,35 @@ int make_window(const kd_sim* s, const kd_obs_spec* sp, ObsWin* w) {
     return KD_OK;
 }
 
-// Observation of the position-space state psi: row sums, forward 2D FFT into work,
-// momentum density, window reduction into out[slot].
+// Observation of the position-space state psi: row sums, forward 2D FFT into work, the
+// window cells' momentum-space values (into the md scratch), window reduction into
+// out[slot].
 int observe_launch(kd_sim* s, const ObsWin& w, int basis, bool in_step, int n_local, double t_fixed,
                    int64_t obs_every, int64_t cap, kd_obs* out) {
     int rc = ensure_md(s);
     if (rc) return rc;
     rc = rowsum_launch(s, s->psi);
     if (rc) return rc;
-    rc = momentum_density_launch(s, basis, s->md);
-    if (rc) return rc;
+    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_NONE, s->psi, s->work, 0, 0.0));
+    KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F1, OP_NONE, s->work, s->work, 0, 0.0));
+    {
+        const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
+        const double dpy = s->u.hbar * 2.0 * kPi / (s->g.y_max - s->g.y_min);
+        const double mc2 = s->u.m * s->u.c * s->u.c;
+        const double cellw = dxdy(s) / (double)s->P;
+        const int ncell = (w.ihi[0] - w.ilo[0] + 1) * (w.jhi[0] - w.jlo[0] + 1) +
+                          (w.ihi[1] - w.ilo[1] + 1) * (w.jhi[1] - w.jlo[1] + 1) + 1;
+        if (s->prec == KD_FP64)
+            k_obs_cells<double><<<grid_blocks(ncell, 128), 128, 0, s->stream>>>(
+                (const double*)s->work, s->g.nx, s->g.ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y,
+                s->u.c, mc2, basis, cellw, w, s->md);
+        else
+            k_obs_cells<float><<<grid_blocks(ncell, 128), 128, 0, s->stream>>>(
+                (const float*)s->work, s->g.nx, s->g.ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y,
+                s->u.c, mc2, basis, cellw, w, s->md);
+        KD_CUDA(cudaGetLastError());
+        ++s->launches;
+    }
     k_obs_reduce<<<1, 256, 0, s->stream>>>(s->rowsum, s->md, s->g.nx, s->g.ny, dxdy(s), w, s->steps,
                                            in_step ? s->clock : nullptr, n_local, t_fixed,
                                            obs_every, cap, out, s->scalar, s->watch_tol, s->status);

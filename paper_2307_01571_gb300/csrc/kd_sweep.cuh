@@ -26,22 +26,30 @@
 #include "kd_internal.h"
 
 // Launch shape of the FP32 sweeps (compile-time; the defaults are the measured best on
-// GB300 for the 1024x512 grid): threads per row CTA, threads per column-tile CTA, the
-// minimum column-tile width, and the resident warps per SM the register budget targets.
+// GB300 for the 1024x512 grid): spinor components per CTA (2: one 2x2 pair, the CTAs of
+// the two pairs run side by side; 4: both pairs share field/table loads), threads per row
+// CTA, threads per column-tile CTA, the minimum column-tile width, and the resident warps
+// per SM the register budget targets.
 #ifndef KD_X_THREADS
 #define KD_X_THREADS 128
 #endif
 #ifndef KD_Y_THREADS
-#define KD_Y_THREADS 512
+#define KD_Y_THREADS 256
 #endif
 #ifndef KD_Y_MINB
-#define KD_Y_MINB 8
+#define KD_Y_MINB 4
+#endif
+#ifndef KD_NC_X
+#define KD_NC_X 2
+#endif
+#ifndef KD_NC_Y
+#define KD_NC_Y 4
 #endif
 #ifndef KD_RESIDENT_WARPS_X
 #define KD_RESIDENT_WARPS_X 28
 #endif
 #ifndef KD_RESIDENT_WARPS_Y
-#define KD_RESIDENT_WARPS_Y 32
+#define KD_RESIDENT_WARPS_Y 16
 #endif
 
 namespace kd {
@@ -172,7 +180,7 @@ template <typename T, int LOGN, int AXIS> struct Cfg {
     static constexpr int N = 1 << LOGN;
     // components per CTA: FP32 CTAs own one 2x2 pair (twice the resident warps at half
     // the registers); FP64 CTAs own both pairs so the costly FP64 field is evaluated once
-    static constexpr int NC = (!F64 || LOGN >= 12) ? 2 : 4;
+    static constexpr int NC = F64 ? (LOGN >= 12 ? 2 : 4) : (AXIS == AXIS_X ? KD_NC_X : KD_NC_Y);
     static constexpr int LOGRMAX = F64 ? (NC == 2 ? 3 : 2) : 3;
     static constexpr int LOGE = LOGN < LOGRMAX ? LOGN : LOGRMAX;
     static constexpr int E = 1 << LOGE;                          // elements per thread
@@ -511,9 +519,22 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
     // same rounded pi and m c as below is unitary to ~1e-11), per row f = e^{i phi} - 1
     // (unit modulus of 1 + f to ~1e-12).  Applied as psi/P + a psi - i b (H0/c) psi, then
     // times 1 + f; each result is a rounding around psi itself, which carries no bias.
-    KD_DI static void op_kinetic(const SweepArgs& a, const Ctx& c, C* v) {
+    // per-point kinetic table entries of this thread (op layout), loaded at kernel start
+    // so that their L2 latency overlaps the first FFT
+    KD_DI static void load_ktab(const SweepArgs& a, const Ctx& c, C* kab) {
         constexpr int R = 1 << LR_OP;
         const C* kt = reinterpret_cast<const C*>(a.ktab);
+#pragma unroll
+        for (int m = 0; m < E / R; ++m)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int ky = c.jt + m * TF + r * (N / R);
+                kab[m * R + r] = c.valid ? __ldcg(kt + (long long)ky * a.nx + c.line) : mk<C>(T(0), T(0));
+            }
+    }
+
+    KD_DI static void op_kinetic(const SweepArgs& a, const Ctx& c, C* v, const C* kab) {
+        constexpr int R = 1 << LR_OP;
         const T pix = __ldg(reinterpret_cast<const T*>(a.kxtab) + c.line);
         T mc, invP;   // invP = 1/P is exact (power of two)
         if constexpr (sizeof(T) == 4) { mc = a.mc_f; invP = a.invP_f; }
@@ -525,7 +546,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int ky = c.jt + m * TF + r * (N / R);
-                const C ab = __ldcg(kt + (long long)ky * a.nx + c.line);
+                const C ab = kab[m * R + r];
                 const T4 yv = kyt[ky];                   // (pi_y, cos phi - 1, sin phi, 0)
                 C* e = v + (m * R + r) * NC;
 #pragma unroll
@@ -562,9 +583,15 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
         c.sm = reinterpret_cast<U*>(smem_raw);
         C v[E * NC];
         load<LR_LOAD>(a, c, v);
-        if constexpr (HAS1) fft<DIR1, false, 0, 0>(a, c, v);
-        if (AXIS == AXIS_X && a.op == OP_POTENTIAL) op_potential(a, c, v);
-        if (AXIS == AXIS_Y && a.op == OP_KINETIC) op_kinetic(a, c, v);
+        if constexpr (AXIS == AXIS_Y) {
+            C kab[E];
+            if (a.op == OP_KINETIC) load_ktab(a, c, kab);
+            if constexpr (HAS1) fft<DIR1, false, 0, 0>(a, c, v);
+            if (a.op == OP_KINETIC) op_kinetic(a, c, v, kab);
+        } else {
+            if constexpr (HAS1) fft<DIR1, false, 0, 0>(a, c, v);
+            if (a.op == OP_POTENTIAL) op_potential(a, c, v);
+        }
         if constexpr (HAS2) fft<DIR2, true, HAS1 ? NST - 1 : 0, 0>(a, c, v);
         store<LR_STORE>(a, c, v);
     }
