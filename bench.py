@@ -36,6 +36,9 @@ FALLBACK_HBM_GBS = 6800.0
 # four-component spinor (x sweep and y sweep)
 BYTES_PER_PT_STEP = {"fp32": 2 * 2 * 4 * 8, "fp64": 2 * 2 * 4 * 16}
 BYTES_PER_PT_SWEEP = {"fp32": 2 * 4 * 8, "fp64": 2 * 4 * 16}
+# FP64 FMA peak of one GB300 (the recipe's nominal 1.25 TFLOP/s; an FMA-chain probe
+# measured 1.256): the FP64 sweeps are bound by this pipe, not by HBM
+FP64_PEAK_TFLOPS = 1.25
 
 
 def parse():
@@ -133,6 +136,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate(ms_local: float, points_per_rank: float, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    points_per_rank grid-point-steps; the job time is the slowest rank's (max over ranks).
+    Returns (grid-point-steps/s, job ms)."""
+    import torch
+    ms = float(ms_local)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        t = torch.tensor([ms], dtype=torch.float64, device=device or "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        world = dist.get_world_size()
+    return points_per_rank * world / (ms * 1e-3), ms
+
+
 def oracle_rate(wl, nsteps: int):
     """The CPU oracle as it stands, single-threaded, on nsteps Strang steps of wl's grid."""
     import oracle
@@ -220,10 +238,7 @@ def main():
         launches = sim.launch_count() - l0
         ck_res = ck.stop() if ck else None
         ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
-        if dist:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        _, ms = aggregate(ms, 0.0, dist, "cuda")
         drift = max(abs(o["norm"] - n0) for o in obs) if obs else None
         # dominant-kernel timing: back-to-back launches of each fused sweep
         sweep_ms = {}
@@ -260,6 +275,19 @@ def main():
         nb = host_in.numel() * host_in.element_size()
         obs_b = len(obs) * 14 * 8
         return wl.points * wl.nsteps * K / dt, nb, nb + obs_b
+
+    def roofline_alu(wl, sweep_ms):
+        # algorithmic FP64 flops per launch: the two 1D FFTs of every line and component
+        # in the 5 N log2 N convention (the potential and kinetic factors not counted)
+        kern = max(sweep_ms, key=sweep_ms.get)
+        n, lines = (wl.grid.nx, wl.grid.ny) if kern == "x_sweep" else (wl.grid.ny, wl.grid.nx)
+        flops = 2 * 4 * lines * 5.0 * n * np.log2(n)
+        ach = flops / (sweep_ms[kern] * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": kern, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "nominal FP64 (1.25 TFLOP/s; 1.256 measured by an FMA probe)",
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "algorithmic_flops_per_launch": flops,
+                "launch_ms": {k: round(v, 5) for k, v in sweep_ms.items()}}
 
     def roofline(form, wl, sweep_ms, hbm_peak):
         kern = max(sweep_ms, key=sweep_ms.get)
@@ -298,7 +326,8 @@ def main():
         v64 = wl64.points * wl64.nsteps * K64 * world / (ms64 * 1e-3)
         line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
                         "norm_drift": drift64, "speedup_fp32_over_fp64": value / v64,
-                        "roofline": roofline("fp64", wl64, sw64, hbm), "gpu_launches": l64}
+                        "roofline": roofline_alu(wl64, sw64),
+                        "roofline_hbm": roofline("fp64", wl64, sw64, hbm), "gpu_launches": l64}
     if rank == 0 and not args.no_cpu:
         # error of both forms against the oracle on the same grid (4 Strang steps), and the
         # oracle's own rate on that sample
