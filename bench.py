@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--strang", type=int, default=2000, help="Strang steps per bench step")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
     return p.parse_args()
 
 
@@ -187,6 +188,49 @@ def run_reference(args):
                          "sample": f"{per} Strang steps of the 1024x512 FP64 run per bench step"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def batched_form(kd, stream, K, barrier, dist):
+    """Config 4: 64 independent seeded Gaussian-beam runs on mixed grids (128x128 to
+    512x256, FP32) advanced by kd_batch_step (one graph launch per 100-step chunk, the
+    runs as concurrent branches), against the same runs one after the other."""
+    import torch
+    members = W.c4()
+    pts = sum(w.points for w in members) * members[0].nsteps
+    sims = [kd.Sim.from_workload(w, stream=stream.cuda_stream) for w in members]
+    for s_, w in zip(sims, members):
+        s_.init_packet(w.packet)
+    dts = [w.dt for w in members]
+    res = {}
+    with kd.Batch(sims, stream=stream.cuda_stream) as b:
+        b.step(dts, members[0].nsteps, obs_every=100)           # warm-up: graphs captured
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            b.step(dts, members[0].nsteps, obs_every=100)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / K
+    for s_, w in zip(sims, members):                           # the same runs one by one
+        s_.step(w.dt, w.nsteps, obs_every=100)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s_, w in zip(sims, members):
+        s_.step(w.dt, w.nsteps, obs_every=100)
+    e1.record(stream)
+    e1.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for s_ in sims:
+        s_.close()
+    value, ms = aggregate(ms, pts, dist, "cuda")
+    res.update({"value": value, "unit": UNIT, "ms_per_step": ms, "steps": K, "sims": len(members),
+                "workload": "64 seeded Gaussian-beam runs, grids 128x128..512x256, c64, "
+                            "2000 steps, observations every 100",
+                "sequential_value": pts / (ms_seq * 1e-3),
+                "speedup_vs_sequential": ms_seq / ms})
+    return res
 
 
 def main():
@@ -328,6 +372,10 @@ def main():
                         "norm_drift": drift64, "speedup_fp32_over_fp64": value / v64,
                         "roofline": roofline_alu(wl64, sw64),
                         "roofline_hbm": roofline("fp64", wl64, sw64, hbm), "gpu_launches": l64}
+    if not args.no_batch:
+        line["batched"] = batched_form(kd, stream, max(1, min(K, 3)), barrier, dist)
+        if "fp64" in line:
+            line["batched"]["speedup_vs_fp64_single"] = line["batched"]["value"] / line["fp64"]["value"]
     if rank == 0 and not args.no_cpu:
         # error of both forms against the oracle on the same grid (4 Strang steps), and the
         # oracle's own rate on that sample

@@ -174,6 +174,22 @@ int kd_set_watchdog(kd_sim* sim, double tol);
 int kd_get_state(kd_sim* sim, void* buf, size_t* size);
 int kd_set_state(kd_sim* sim, const void* buf, size_t size);
 
+/* Batched form: several independent simulations (any grid sizes and precisions, one
+ * device) advanced together.  kd_batch_step runs the same Strang-step schedule as kd_step
+ * for every simulation, each with its own dt[i], as one CUDA-graph launch per chunk of
+ * steps in which each simulation's sweeps form an independent branch, so that the
+ * simulations' kernels run concurrently.  Observation records go to
+ * obs_out[i * obs_cap + j] (host memory); *n_obs receives the count per simulation.  The
+ * batch borrows the simulations: between batch calls they may be used on their own, but
+ * not during one (a batch call orders all their work on cuda_stream).  Returns the first
+ * error of any simulation (the others are still advanced).  The batch holds no buffers of
+ * its own besides its graphs. */
+typedef struct kd_batch kd_batch;
+int kd_batch_create(kd_sim* const* sims, int32_t n, void* cuda_stream, kd_batch** out);
+int kd_batch_step(kd_batch* batch, const double* dt, int64_t nsteps, int64_t obs_every,
+                  kd_obs* obs_out, int64_t obs_cap, int64_t* n_obs);
+void kd_batch_destroy(kd_batch* batch);
+
 /* Benchmark hook: enqueues `reps` back-to-back launches of one fused sweep on the
  * simulation's stream, in place on the current state, and returns without waiting.
  * kind 0 = x sweep (inverse x-FFT, full potential step exp(-i dt V(t)/hbar), forward

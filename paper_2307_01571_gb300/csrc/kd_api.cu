@@ -107,6 +107,7 @@ struct kd_sim {
     double watch_tol = 0.0;
     // graphs of the step loop; cleared whenever a captured argument changes
     std::map<GraphKey, std::pair<cudaGraphExec_t, int64_t>> graphs;  // exec, kernel nodes
+    uint64_t graph_gen = 0;   // incremented whenever captured arguments change
     int64_t launches = 0;
     int64_t graph_obs_every = -1, graph_obs_cap = -1;
     double graph_dt = 0.0, graph_t0 = 0.0;
@@ -125,6 +126,7 @@ double dxdy(const kd_sim* s) {
 void clear_graphs(kd_sim* s) {
     for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second.first);
     s->graphs.clear();
+    ++s->graph_gen;
 }
 
 // ---------------------------------------------------------------- small kernels ---
@@ -1099,20 +1101,31 @@ int kd_init_packet(kd_sim* s, const kd_packet* pk) {
     return KD_OK;
 }
 
-int kd_step(kd_sim* s, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs_out,
-            int64_t obs_cap, int64_t* n_obs) {
-    int rc = check_sim(s);
-    if (rc) return rc;
-    if (n_obs) *n_obs = 0;
+}  // extern "C"
+
+namespace {
+
+// One kd_step call's parameters after validation.
+struct StepPlan {
+    double dt;
+    int64_t nsteps, obs_every, nobs, cap;
+    ObsWin w;
+};
+
+// Validates the arguments, rebases the clock, (re)builds the dt tables and buffers, and
+// drops cached graphs whose captured arguments changed.  No device work is enqueued
+// except the table build.
+int prepare_step(kd_sim* s, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs_out,
+                 int64_t obs_cap, StepPlan* plan) {
     if (!(dt > 0) || !isfinite(dt)) return fail(KD_ERR_ARG, "dt must be positive and finite");
     if (nsteps < 0 || obs_every < 0 || obs_cap < 0) return fail(KD_ERR_ARG, "negative count");
     if (nsteps > (int64_t)1 << 40) return fail(KD_ERR_ARG, "nsteps too large");
     if (obs_every > 0 && obs_cap > 0 && !obs_out) return fail(KD_ERR_ARG, "obs_out is null");
     if (obs_every > 0 && !s->has_spec) return fail(KD_ERR_ARG, "no observation spec: call kd_init_packet or kd_set_obs_spec");
-    if (nsteps == 0) return KD_OK;
-    ObsWin w{};
+    plan->w = ObsWin{};
+    int rc;
     if (obs_every > 0) {
-        rc = make_window(s, &s->spec, &w);
+        rc = make_window(s, &s->spec, &plan->w);
         if (rc) return rc;
     }
     // rebase the clock when dt changes: t = t0 + step * dt
@@ -1136,67 +1149,261 @@ int kd_step(kd_sim* s, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs
         if (rc) return rc;
     }
     if (obs_every != s->graph_obs_every || cap != s->graph_obs_cap || dt != s->graph_dt ||
-        s->t0 != s->graph_t0 || memcmp(&w, &s->graph_win, sizeof w) != 0) {
+        s->t0 != s->graph_t0 || memcmp(&plan->w, &s->graph_win, sizeof plan->w) != 0) {
         clear_graphs(s);
         s->graph_obs_every = obs_every;
         s->graph_obs_cap = cap;
         s->graph_dt = dt;
         s->graph_t0 = s->t0;
-        s->graph_win = w;
+        s->graph_win = plan->w;
     }
+    plan->dt = dt;
+    plan->nsteps = nsteps;
+    plan->obs_every = obs_every;
+    plan->nobs = nobs;
+    plan->cap = cap;
+    return KD_OK;
+}
+
+// Per-call device work before the step loop: per-step scalars, clock, watchdog
+// reference, and the opening half step of the first step (t_0).
+int enqueue_prologue(kd_sim* s, const StepPlan& p) {
     const double omega = s->u.c * s->f.k_L;
-    k_step_scalars<<<grid_blocks((size_t)nsteps + 1, 256), 256, 0, s->stream>>>(
-        s->steps, nsteps, s->t0, s->step, dt, s->f.a0, omega, s->f.phase0, s->f.env_T, s->f.box_vy,
-        s->g.y_min);
+    k_step_scalars<<<grid_blocks((size_t)p.nsteps + 1, 256), 256, 0, s->stream>>>(
+        s->steps, p.nsteps, s->t0, s->step, p.dt, s->f.a0, omega, s->f.phase0, s->f.env_T,
+        s->f.box_vy, s->g.y_min);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
     k_set_clock<<<1, 1, 0, s->stream>>>(s->clock, 0);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
-    if (nobs > 0) {
+    if (p.nobs > 0) {
         KD_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), s->stream));
         if (s->watch_tol > 0) {
-            rc = rowsum_launch(s, s->psi);
+            int rc = rowsum_launch(s, s->psi);
             if (rc) return rc;
             k_norm<<<1, 256, 0, s->stream>>>(s->rowsum, s->g.ny, dxdy(s), s->scalar, 1);
             KD_CUDA(cudaGetLastError());
-    ++s->launches;
+            ++s->launches;
         }
     }
-    // opening half step of the first step (t_0)
-    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_POTENTIAL, s->psi, s->psi, 0, 0.5 * dt));
-    const int64_t chunk_n = obs_every > 0 ? obs_every : 64;
+    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_POTENTIAL, s->psi, s->psi, 0, 0.5 * p.dt));
+    return KD_OK;
+}
+
+// The chunks of a call: chunk i covers steps [i c, (i + 1) c) with c = obs_every (or 64
+// without observations); fn(chunk, last, obs) enqueues or launches one chunk.
+template <typename F> int for_each_chunk(const StepPlan& p, F fn) {
+    const int64_t chunk_n = p.obs_every > 0 ? p.obs_every : 64;
     int64_t done = 0;
-    while (done < nsteps) {
-        const int64_t left = nsteps - done;
-        const int chunk = (int)(left < chunk_n ? left : chunk_n);
-        const bool last = done + chunk == nsteps;
-        const bool obs = obs_every > 0 && chunk == obs_every;
+    while (done < p.nsteps) {
+        const int64_t left = p.nsteps - done;
+        const int64_t chunk = left < chunk_n ? left : chunk_n;
+        const bool last = done + chunk == p.nsteps;
+        const bool obs = p.obs_every > 0 && chunk == p.obs_every;
+        int rc = KD_OK;
         if (chunk <= 4096) {
-            rc = run_chunk(s, dt, chunk, last, obs, w, obs_every, cap);
+            rc = fn((int)chunk, last, obs);
         } else {  // very long chunks without observations run in pieces of 64
-            rc = KD_OK;
             int64_t rem = chunk;
             while (rem > 0 && rc == KD_OK) {
                 const int c2 = (int)(rem < 64 ? rem : 64);
-                rc = run_chunk(s, dt, c2, last && rem == c2, false, w, obs_every, cap);
+                rc = fn(c2, last && rem == c2, false);
                 rem -= c2;
             }
         }
         if (rc) return rc;
         done += chunk;
     }
-    s->step += nsteps;
-    if (nobs > 0) {
-        if (cap > 0) KD_CUDA(cudaMemcpyAsync(obs_out, s->obs_dev, cap * sizeof(kd_obs), cudaMemcpyDeviceToHost, s->stream));
+    return KD_OK;
+}
+
+// After the loop: copy the observation records (synchronises the stream) and turn the
+// watchdog status into a return code.
+int finish_step(kd_sim* s, const StepPlan& p, kd_obs* obs_out, int64_t* n_obs) {
+    s->step += p.nsteps;
+    if (p.nobs > 0) {
+        if (p.cap > 0)
+            KD_CUDA(cudaMemcpyAsync(obs_out, s->obs_dev, p.cap * sizeof(kd_obs), cudaMemcpyDeviceToHost, s->stream));
         int st = 0;
         KD_CUDA(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
         KD_CUDA(cudaStreamSynchronize(s->stream));
-        if (n_obs) *n_obs = nobs;
+        if (n_obs) *n_obs = p.nobs;
         if (st & 1) return fail(KD_ERR_NONFINITE, "non-finite norm observed");
         if (st & 2) return fail(KD_ERR_NORM_DRIFT, "norm drift beyond %g", s->watch_tol);
     }
     return KD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kd_step(kd_sim* s, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs_out,
+            int64_t obs_cap, int64_t* n_obs) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (n_obs) *n_obs = 0;
+    StepPlan p;
+    rc = prepare_step(s, dt, nsteps, obs_every, obs_out, obs_cap, &p);
+    if (rc || nsteps == 0) return rc;
+    rc = enqueue_prologue(s, p);
+    if (rc) return rc;
+    rc = for_each_chunk(p, [&](int chunk, bool last, bool obs) {
+        return run_chunk(s, p.dt, chunk, last, obs, p.w, p.obs_every, p.cap);
+    });
+    if (rc) return rc;
+    return finish_step(s, p, obs_out, n_obs);
+}
+
+}  // extern "C"
+
+struct kd_batch {
+    std::vector<kd_sim*> sims;
+    cudaStream_t stream = nullptr;   // caller's stream
+    cudaStream_t cap = nullptr;      // capture origin
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    int device = 0;
+    // one graph per chunk shape: all simulations' chunks as concurrent branches
+    std::map<GraphKey, std::pair<cudaGraphExec_t, std::vector<int64_t>>> graphs;
+    std::vector<uint64_t> gens;      // simulations' graph generations the graphs were built on
+};
+
+namespace {
+
+void clear_batch_graphs(kd_batch* b) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.first);
+    b->graphs.clear();
+}
+
+// Runs fn(sim, i) with every simulation's work forked from `origin` onto the
+// simulation's own capture stream and joined back, so that the simulations' kernels are
+// independent branches (of a capture, or of the stream graph).
+template <typename F> int fork_join(kd_batch* b, cudaStream_t origin, F fn) {
+    KD_CUDA(cudaEventRecord(b->fork, origin));
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        kd_sim* s = b->sims[i];
+        KD_CUDA(cudaStreamWaitEvent(s->cap_stream, b->fork, 0));
+        cudaStream_t saved = s->stream;
+        s->stream = s->cap_stream;
+        int rc = fn(s, i);
+        s->stream = saved;
+        if (rc) return rc;
+        KD_CUDA(cudaEventRecord(b->join[i], s->cap_stream));
+        KD_CUDA(cudaStreamWaitEvent(origin, b->join[i], 0));
+    }
+    return KD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kd_batch_create(kd_sim* const* sims, int32_t n, void* cuda_stream, kd_batch** out) {
+    g_err.clear();
+    if (!sims || !out || n <= 0) return fail(KD_ERR_ARG, "need n > 0 simulations and an output pointer");
+    *out = nullptr;
+    int dev = -1;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!sims[i]) return fail(KD_ERR_ARG, "simulation %d is null", i);
+        if (dev >= 0 && sims[i]->device != dev) return fail(KD_ERR_ARG, "simulations live on different devices");
+        dev = sims[i]->device;
+        for (int32_t j = 0; j < i; ++j)
+            if (sims[j] == sims[i]) return fail(KD_ERR_ARG, "simulation %d appears twice", i);
+    }
+    KD_CUDA(cudaSetDevice(dev));
+    kd_batch* b = new kd_batch();
+    b->sims.assign(sims, sims + n);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->device = dev;
+    b->join.assign(n, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int32_t i = 0; ok && i < n; ++i)
+        ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        kd_batch_destroy(b);
+        return fail(KD_ERR_CUDA, "stream/event creation failed");
+    }
+    b->gens.assign(n, ~0ull);
+    *out = b;
+    return KD_OK;
+}
+
+void kd_batch_destroy(kd_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    clear_batch_graphs(b);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+int kd_batch_step(kd_batch* b, const double* dt, int64_t nsteps, int64_t obs_every,
+                  kd_obs* obs_out, int64_t obs_cap, int64_t* n_obs) {
+    if (!b || !dt) return fail(KD_ERR_ARG, "null batch or dt");
+    KD_CUDA(cudaSetDevice(b->device));
+    if (n_obs) *n_obs = 0;
+    const size_t n = b->sims.size();
+    std::vector<StepPlan> plans(n);
+    for (size_t i = 0; i < n; ++i) {
+        int rc = prepare_step(b->sims[i], dt[i], nsteps, obs_every,
+                              obs_out ? obs_out + i * (size_t)obs_cap : nullptr, obs_cap, &plans[i]);
+        if (rc) return rc;
+    }
+    if (nsteps == 0) return KD_OK;
+    for (size_t i = 0; i < n; ++i)
+        if (b->gens[i] != b->sims[i]->graph_gen) {
+            clear_batch_graphs(b);
+            for (size_t k = 0; k < n; ++k) b->gens[k] = b->sims[k]->graph_gen;
+            break;
+        }
+    int rc = fork_join(b, b->stream, [&](kd_sim* s, size_t i) { return enqueue_prologue(s, plans[i]); });
+    if (rc) return rc;
+    rc = for_each_chunk(plans[0], [&](int chunk, bool last, bool obs) -> int {
+        GraphKey key{chunk, last ? 1 : 0, obs ? 1 : 0};
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            std::vector<int64_t> nodes(n, 0);
+            cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return fail(KD_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+            int crc = fork_join(b, b->cap, [&](kd_sim* s, size_t i) {
+                const int64_t before = s->launches;
+                int r = enqueue_chunk(s, plans[i].dt, chunk, last, obs, plans[i].w, plans[i].obs_every,
+                                      plans[i].cap);
+                nodes[i] = s->launches - before;
+                s->launches = before;
+                return r;
+            });
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(b->cap, &graph);
+            if (crc) { if (graph) cudaGraphDestroy(graph); return crc; }
+            if (e != cudaSuccess) return fail(KD_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(KD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            it = b->graphs.emplace(key, std::make_pair(exec, nodes)).first;
+        }
+        KD_CUDA(cudaGraphLaunch(it->second.first, b->stream));
+        for (size_t i = 0; i < n; ++i) b->sims[i]->launches += it->second.second[i];
+        return KD_OK;
+    });
+    if (rc) return rc;
+    int first_err = KD_OK;
+    for (size_t i = 0; i < n; ++i) {
+        kd_sim* s = b->sims[i];
+        cudaStream_t saved = s->stream;
+        s->stream = b->stream;   // all branches are joined on the batch stream
+        int r = finish_step(s, plans[i], obs_out ? obs_out + i * (size_t)obs_cap : nullptr, n_obs);
+        s->stream = saved;
+        if (r && !first_err) first_err = r;
+    }
+    return first_err;
 }
 
 int kd_observe(kd_sim* s, const kd_obs_spec* spec, kd_obs* out) {

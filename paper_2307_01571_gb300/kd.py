@@ -94,6 +94,10 @@ _SIGS = {
     "kd_get_launch_count": (C.c_int, [_vp, _P(C.c_int64)]),
     "kd_density_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                      C.c_double, _vp, _vp, _vp]),
+    "kd_batch_create": (C.c_int, [_P(_vp), C.c_int32, _vp, _P(_vp)]),
+    "kd_batch_step": (C.c_int, [_vp, _P(C.c_double), C.c_int64, C.c_int64, _P(kd_obs), C.c_int64,
+                                _P(C.c_int64)]),
+    "kd_batch_destroy": (None, [_vp]),
     "kd_destroy": (None, [_vp]),
     "kd_last_error": (C.c_char_p, []),
     "kd_version": (C.c_int, []),
@@ -245,3 +249,43 @@ class Sim:
     def set_state(self, blob: bytes):
         buf = (C.c_char * len(blob)).from_buffer_copy(blob)
         _check(kd_set_state(self._h, buf, len(blob)))
+
+
+class Batch:
+    """Several simulations advanced together by one graph launch per chunk of steps
+    (``kd_batch_*``)."""
+
+    def __init__(self, sims, stream: int | None = None):
+        self.sims = list(sims)
+        arr = (_vp * len(self.sims))(*[s.handle for s in self.sims])
+        h = _vp()
+        _check(kd_batch_create(arr, len(self.sims), _vp(stream) if stream else None, C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            kd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, dts, nsteps: int, obs_every: int = 0):
+        n = len(self.sims)
+        nobs = nsteps // obs_every if obs_every > 0 else 0
+        dt_arr = (C.c_double * n)(*[float(d) for d in dts])
+        buf = (kd_obs * max(n * nobs, 1))()
+        got = C.c_int64()
+        _check(kd_batch_step(self._h, dt_arr, nsteps, obs_every, buf if nobs > 0 else None, nobs,
+                             C.byref(got)))
+        return [[{k: getattr(buf[i * nobs + j], k) for k in OBS_FIELDS} for j in range(nobs)]
+                for i in range(n)]

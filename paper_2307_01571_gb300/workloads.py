@@ -194,6 +194,34 @@ def small(nx: int, ny: int, kind: int = GAUSS, units: Units = NATURAL, nsteps: i
                     precision=precision)
 
 
+def c4(units: Units = ATOMIC, n: int = 64, seed: int = 0, nsteps: int = 2000,
+       precision: int = FP32) -> list:
+    """Batched form: n independent Gaussian-beam runs with seeded parameters.  Grid per run
+    uniform from {128x128, 256x128, 256x256, 512x256} over (nx/16) x (ny/16) wavelengths,
+    waist U[5, 20] wavelengths, a0 log-uniform in [1e-2, 0.4], sin^2 envelope
+    U[100, 2000] steps, spin +-1 along x, p0 = (-hbar k_L, m c), box moving at c/sqrt 2."""
+    rng = np.random.default_rng(seed)
+    k, lam = laser(units)
+    dt = dt_of(units)
+    shapes = [(128, 128), (256, 128), (256, 256), (512, 256)]
+    out = []
+    for i in range(n):
+        nx, ny = shapes[int(rng.integers(0, len(shapes)))]
+        w0 = float(rng.uniform(5.0, 20.0)) * lam
+        a0 = float(np.exp(rng.uniform(np.log(1e-2), np.log(0.4))))
+        env = float(rng.uniform(100.0, 2000.0)) * dt
+        spin = int(rng.choice([1, -1]))
+        Lx, Ly = nx / 16 * lam, ny / 16 * lam
+        g = Grid(nx, ny, -Lx / 2, Lx / 2, -Ly / 2, Ly / 2)
+        f = Field(kind=GAUSS, longitudinal=1, a0=a0, k_L=k, epsilon=1.0 / (k * w0), env_T=env,
+                  p_shift_x=0.0, p_shift_y=units.mc, box_vy=units.c / math.sqrt(2.0))
+        p = Packet(-units.hbar * k, units.mc, 0.0, 0.0, units.hbar * k * 16 / min(nx, ny), spin, 0)
+        out.append(Workload(f"batch member {i}: {nx}x{ny}", units, g, f, p, dt, nsteps,
+                            obs_every=100, precision=precision,
+                            extra={"w0_lambda": w0 / lam, "a0": a0, "env_steps": env / dt}))
+    return out
+
+
 def random_spinor(nx: int, ny: int, seed: int) -> np.ndarray:
     """Seeded complex Gaussian spinor, shape (ny, nx, 4), unit sum of |psi|^2."""
     rng = np.random.default_rng(seed)
