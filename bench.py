@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-surrogate", action="store_true")
     return p.parse_args()
 
 
@@ -233,6 +234,31 @@ def batched_form(kd, stream, K, barrier, dist):
     return res
 
 
+def surrogate_form(n_runs: int = 4096):
+    """Config 5: the MLP surrogate (5 -> 3 x 256 GELU -> 4) trained by the library's own
+    kernels on n_runs batched-solver runs (seeded uniform draws, 256x128, 2000 steps),
+    90/10 split; held-out error in log10 decades and time per prediction vs per run."""
+    from paper_2307_01571_gb300 import surrogate as S
+    X = S.draw_params(n_runs, seed=1)
+    Y, secs = S.solve(X, batch=512)
+    n_tr = int(0.9 * n_runs)
+    sur = S.Surrogate(seed=0)
+    t_fit = sur.fit(X[:n_tr], Y[:n_tr], steps=4000, batch=256, lr=2e-3)
+    pred = sur.predict(X[n_tr:])
+    t0 = time.perf_counter()
+    for _ in range(20):
+        sur.predict(X[n_tr:])
+    t_pred = (time.perf_counter() - t0) / (20 * (n_runs - n_tr))
+    err = S.heldout_error(pred, Y[n_tr:])
+    base = S.heldout_error(np.tile(Y[:n_tr].mean(0), (n_runs - n_tr, 1)), Y[n_tr:])
+    return {"runs": n_runs, "train": n_tr, "heldout": n_runs - n_tr,
+            "solver_s_per_run_batched": secs / n_runs, "train_s": t_fit,
+            "predict_s_per_sample": t_pred, "speedup_vs_solver": secs / n_runs / t_pred,
+            "heldout_rms_log10": {k: v["rms"] for k, v in err.items()},
+            "heldout_max_log10": {k: v["max"] for k, v in err.items()},
+            "constant_predictor_rms_log10": {k: v["rms"] for k, v in base.items()}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -376,6 +402,8 @@ def main():
         line["batched"] = batched_form(kd, stream, max(1, min(K, 3)), barrier, dist)
         if "fp64" in line:
             line["batched"]["speedup_vs_fp64_single"] = line["batched"]["value"] / line["fp64"]["value"]
+    if rank == 0 and not args.no_surrogate:
+        line["surrogate"] = surrogate_form()
     if rank == 0 and not args.no_cpu:
         # error of both forms against the oracle on the same grid (4 Strang steps), and the
         # oracle's own rate on that sample

@@ -190,6 +190,28 @@ int kd_batch_step(kd_batch* batch, const double* dt, int64_t nsteps, int64_t obs
                   kd_obs* obs_out, int64_t obs_cap, int64_t* n_obs);
 void kd_batch_destroy(kd_batch* batch);
 
+/* Surrogate network (BASELINE's learned part; the paper has no network): a fully
+ * connected MLP, widths[0] inputs -> ... -> widths[nlayers] outputs, exact-erf GELU on the
+ * hidden layers, linear output, trained with mean squared error and Adam
+ * (beta = 0.9, 0.999, eps = 1e-8) by hand-written FP32 kernels; every reduction runs in a
+ * fixed order (bitwise reproducible).  Parameters are laid out per layer as W_l
+ * [widths[l+1]][widths[l]] row-major followed by b_l; the caller initialises them
+ * (kd_mlp_set_params, which also resets Adam).  Row-major float batches [batch][width].
+ * kd_mlp_train_step takes device pointers and is asynchronous on cuda_stream; loss_dev
+ * (device, may be NULL) receives the batch loss before the update. */
+typedef struct kd_mlp kd_mlp;
+int kd_mlp_create(const int32_t* widths, int32_t nlayers, kd_mlp** out);
+int kd_mlp_num_params(kd_mlp* net, int64_t* count);
+int kd_mlp_set_params(kd_mlp* net, const float* params, int32_t where);
+int kd_mlp_get_params(kd_mlp* net, float* params, int32_t where);
+int kd_mlp_forward(kd_mlp* net, const float* x, int32_t batch, float* y, int32_t where,
+                   void* cuda_stream);
+int kd_mlp_gradients(kd_mlp* net, const float* x, const float* targets, int32_t batch,
+                     float* loss, float* grads, int32_t where, void* cuda_stream);
+int kd_mlp_train_step(kd_mlp* net, const float* x, const float* targets, int32_t batch,
+                      float lr, float* loss_dev, void* cuda_stream);
+void kd_mlp_destroy(kd_mlp* net);
+
 /* Benchmark hook: enqueues `reps` back-to-back launches of one fused sweep on the
  * simulation's stream, in place on the current state, and returns without waiting.
  * kind 0 = x sweep (inverse x-FFT, full potential step exp(-i dt V(t)/hbar), forward

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkd.so")
-SOURCES = ["kd_api.cu", "kd_sweep_f32.cu", "kd_sweep_f64.cu", "kd_noalloc.cu"]
+SOURCES = ["kd_api.cu", "kd_sweep_f32.cu", "kd_sweep_f64.cu", "kd_noalloc.cu", "kd_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{os.path.join(ROOT, 'include')}"]

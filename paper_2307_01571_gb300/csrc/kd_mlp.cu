@@ -1,0 +1,382 @@
+// kd_mlp.cu -- the surrogate network: a fully connected MLP with exact-erf GELU hidden
+// layers, trained on the batched solver's outputs (seeded parameter draws -> diffraction
+// and spin-flip populations).  Hand-written FP32 kernels: tiled GEMM with fused bias /
+// GELU epilogue, the GELU derivative, fixed-order column sums, MSE loss and Adam.
+// Every reduction runs in a fixed order, so training is bitwise reproducible.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <vector>
+
+#include "../../include/kd.h"
+
+namespace kd {
+int set_error(int code, const char* msg);  // kd_api.cu
+}
+
+struct kd_mlp {
+    int device = 0;
+    int L = 0;                       // number of layers (weight matrices)
+    std::vector<int> w;              // widths, L + 1 entries
+    std::vector<size_t> woff, boff;  // parameter offsets of W_l [w[l+1]][w[l]] and b_l
+    size_t nparam = 0;
+    float* param = nullptr;          // all W and b
+    float* grad = nullptr;
+    float* m1 = nullptr;             // Adam moments
+    float* m2 = nullptr;
+    long long adam_t = 0;
+    int cap = 0;                     // batch capacity of the activation buffers
+    std::vector<float*> z;           // pre-activations per layer [cap][w[l+1]]
+    std::vector<float*> a;           // activations per layer output [cap][w[l+1]] (a[0] = input)
+    float* dbuf0 = nullptr;          // gradient ping-pong buffers [cap][max width]
+    float* dbuf1 = nullptr;
+    float* lossbuf = nullptr;        // [cap * w[L]] squared errors, then partials
+};
+
+namespace {
+
+int err(int code, const char* msg) { return kd::set_error(code, msg); }
+
+#define MLP_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) return err(e_ == cudaErrorMemoryAllocation ? KD_ERR_NOMEM : KD_ERR_CUDA, #call); \
+    } while (0)
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// C[m][n] = sum_k A(m, k) B(k, n) (+ bias[n]; GELU) with A(m, k) = A[m sam + k sak] and
+// B(k, n) = B[k sbk + n sbn].  64x64 tiles, 16-deep k slabs, 256 threads, 4x4 outputs
+// per thread; the k loop runs in order (deterministic).  epi: 0 store, 1 bias, 2 bias
+// then Z = C, Y = GELU(C).
+__global__ void __launch_bounds__(256) k_gemm(const float* A, long sam, long sak, const float* B,
+                                              long sbk, long sbn, float* C, float* Y, const float* bias,
+                                              int M, int N, int K, int epi) {
+    __shared__ float As[16][64 + 1];
+    __shared__ float Bs[16][64 + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4] = {{0}};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            const int kk = e / 64, mm = e % 64;
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < K) ? A[gm * sam + gk * sak] : 0.0f;
+            const int gn = n0 + mm;
+            Bs[kk][mm] = (gk < K && gn < N) ? B[gk * sbk + gn * sbn] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+            if (m >= M || n >= N) continue;
+            float v = acc[i][j];
+            if (epi >= 1) v += bias[n];
+            C[(long)m * N + n] = v;
+            if (epi == 2) Y[(long)m * N + n] = gelu(v);
+        }
+}
+
+// dZ = dY * GELU'(Z), elementwise
+__global__ void k_gelu_back(const float* dY, const float* Z, float* dZ, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dZ[i] = dY[i] * gelu_grad(Z[i]);
+}
+
+// db[n] = sum_m dZ[m][n], rows in order (one thread per column)
+__global__ void k_colsum(const float* dZ, int M, int N, float* db) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int m = 0; m < M; ++m) s += dZ[(long)m * N + n];
+    db[n] = s;
+}
+
+// MSE over B x D outputs: dY = 2 (Y - T) / (B D), sq[i] = (Y - T)^2
+__global__ void k_mse(const float* Y, const float* T, float* dY, float* sq, long n, float scale) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float d = Y[i] - T[i];
+        dY[i] = scale * d;
+        sq[i] = d * d;
+    }
+}
+
+// fixed-order sum of n floats times scale into out[0] (one block)
+__global__ void k_sum(const float* x, long n, float scale, float* out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = (float)(red[0] * scale);
+}
+
+__global__ void k_adam(float* p, const float* g, float* m1, float* m2, long n, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float a = b1 * m1[i] + (1.0f - b1) * gi;
+        const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
+        m1[i] = a;
+        m2[i] = b;
+        p[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+    }
+}
+
+cudaError_t gemm(const float* A, long sam, long sak, const float* B, long sbk, long sbn, float* C,
+                 float* Y, const float* bias, int M, int N, int K, int epi, cudaStream_t s) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    k_gemm<<<grid, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, C, Y, bias, M, N, K, epi);
+    return cudaGetLastError();
+}
+
+int maxw(const kd_mlp* n) {
+    int m = 0;
+    for (int v : n->w) m = v > m ? v : m;
+    return m;
+}
+
+int ensure_cap(kd_mlp* n, int batch) {
+    if (batch <= n->cap) return KD_OK;
+    for (float* p : n->z) cudaFree(p);
+    for (size_t l = 1; l < n->a.size(); ++l) cudaFree(n->a[l]);
+    cudaFree(n->dbuf0);
+    cudaFree(n->dbuf1);
+    cudaFree(n->lossbuf);
+    n->z.assign(n->L, nullptr);
+    n->a.assign(n->L + 1, nullptr);
+    for (int l = 0; l < n->L; ++l) {
+        MLP_CUDA(cudaMalloc(&n->z[l], sizeof(float) * (size_t)batch * n->w[l + 1]));
+        MLP_CUDA(cudaMalloc(&n->a[l + 1], sizeof(float) * (size_t)batch * n->w[l + 1]));
+    }
+    MLP_CUDA(cudaMalloc(&n->dbuf0, sizeof(float) * (size_t)batch * maxw(n)));
+    MLP_CUDA(cudaMalloc(&n->dbuf1, sizeof(float) * (size_t)batch * maxw(n)));
+    MLP_CUDA(cudaMalloc(&n->lossbuf, sizeof(float) * ((size_t)batch * n->w[n->L] + 1)));
+    n->cap = batch;
+    return KD_OK;
+}
+
+// forward pass from device input x (batch rows): a[l+1] = act(a[l] W_l^T + b_l); the
+// last layer is linear (its output is a[L])
+int forward(kd_mlp* n, const float* x, int batch, cudaStream_t s) {
+    n->a[0] = const_cast<float*>(x);
+    for (int l = 0; l < n->L; ++l) {
+        const int fi = n->w[l], fo = n->w[l + 1];
+        const bool last = l == n->L - 1;
+        float* out = last ? n->a[l + 1] : n->z[l];
+        MLP_CUDA(gemm(n->a[l], fi, 1, n->param + n->woff[l], 1, fi, out, last ? nullptr : n->a[l + 1],
+                      n->param + n->boff[l], batch, fo, fi, last ? 1 : 2, s));
+    }
+    return KD_OK;
+}
+
+// loss and gradients for targets t (device): returns via lossbuf[0] the mean squared error
+int backward(kd_mlp* n, const float* t, int batch, cudaStream_t s) {
+    const int D = n->w[n->L];
+    const long nout = (long)batch * D;
+    float* sq = n->lossbuf + 1;
+    k_mse<<<(int)((nout + 255) / 256), 256, 0, s>>>(n->a[n->L], t, n->dbuf0, sq, nout, 2.0f / (float)nout);
+    MLP_CUDA(cudaGetLastError());
+    k_sum<<<1, 256, 0, s>>>(sq, nout, 1.0f / (float)nout, n->lossbuf);   // mean squared error
+    MLP_CUDA(cudaGetLastError());
+    float* dcur = n->dbuf0;   // gradient w.r.t. the output of layer l (pre-activation for the last)
+    float* dnext = n->dbuf1;
+    for (int l = n->L - 1; l >= 0; --l) {
+        const int fi = n->w[l], fo = n->w[l + 1];
+        if (l != n->L - 1) {   // through the GELU: dZ = dA * GELU'(Z)
+            const long cnt = (long)batch * fo;
+            k_gelu_back<<<(int)((cnt + 255) / 256), 256, 0, s>>>(dcur, n->z[l], dcur, cnt);
+            MLP_CUDA(cudaGetLastError());
+        }
+        // dW_l[o][i] = sum_b dZ[b][o] a_l[b][i];  db_l[o] = sum_b dZ[b][o]
+        MLP_CUDA(gemm(dcur, 1, fo, n->a[l], fi, 1, n->grad + n->woff[l], nullptr, nullptr, fo, fi, batch, 0, s));
+        k_colsum<<<(fo + 127) / 128, 128, 0, s>>>(dcur, batch, fo, n->grad + n->boff[l]);
+        MLP_CUDA(cudaGetLastError());
+        if (l > 0) {  // dA_{l}[b][i] = sum_o dZ[b][o] W_l[o][i]
+            MLP_CUDA(gemm(dcur, fo, 1, n->param + n->woff[l], fi, 1, dnext, nullptr, nullptr, batch, fi, fo, 0, s));
+            float* tmp = dcur;
+            dcur = dnext;
+            dnext = tmp;
+        }
+    }
+    return KD_OK;
+}
+
+int copy_io(void* dst, const void* src, size_t bytes, int32_t where_dst, int32_t where_src, cudaStream_t s) {
+    cudaMemcpyKind k = where_src == KD_HOST ? (where_dst == KD_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice)
+                                            : (where_dst == KD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+    MLP_CUDA(cudaMemcpyAsync(dst, src, bytes, k, s));
+    return KD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kd_mlp_create(const int32_t* widths, int32_t nlayers, kd_mlp** out) {
+    if (!widths || !out || nlayers < 1 || nlayers > 16) return err(KD_ERR_ARG, "kd_mlp_create: need 1..16 layers");
+    for (int i = 0; i <= nlayers; ++i)
+        if (widths[i] < 1 || widths[i] > 4096) return err(KD_ERR_ARG, "kd_mlp_create: widths must be in [1, 4096]");
+    *out = nullptr;
+    kd_mlp* n = new kd_mlp();
+    if (cudaGetDevice(&n->device) != cudaSuccess) { delete n; return err(KD_ERR_CUDA, "kd_mlp_create: no CUDA device"); }
+    n->L = nlayers;
+    n->w.assign(widths, widths + nlayers + 1);
+    size_t off = 0;
+    for (int l = 0; l < nlayers; ++l) {
+        n->woff.push_back(off);
+        off += (size_t)n->w[l + 1] * n->w[l];
+        n->boff.push_back(off);
+        off += n->w[l + 1];
+    }
+    n->nparam = off;
+    auto bail = [&](int rc) { kd_mlp_destroy(n); return rc; };
+    if (cudaMalloc(&n->param, off * sizeof(float)) != cudaSuccess || cudaMalloc(&n->grad, off * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&n->m1, off * sizeof(float)) != cudaSuccess || cudaMalloc(&n->m2, off * sizeof(float)) != cudaSuccess)
+        return bail(err(KD_ERR_NOMEM, "kd_mlp_create: allocation failed"));
+    if (cudaMemset(n->param, 0, off * sizeof(float)) != cudaSuccess || cudaMemset(n->m1, 0, off * sizeof(float)) != cudaSuccess ||
+        cudaMemset(n->m2, 0, off * sizeof(float)) != cudaSuccess || cudaMemset(n->grad, 0, off * sizeof(float)) != cudaSuccess)
+        return bail(err(KD_ERR_CUDA, "kd_mlp_create: memset failed"));
+    n->a.assign(nlayers + 1, nullptr);
+    n->z.assign(nlayers, nullptr);
+    *out = n;
+    return KD_OK;
+}
+
+void kd_mlp_destroy(kd_mlp* n) {
+    if (!n) return;
+    cudaSetDevice(n->device);
+    cudaDeviceSynchronize();
+    for (float* p : n->z) cudaFree(p);
+    for (size_t l = 1; l < n->a.size(); ++l) cudaFree(n->a[l]);
+    cudaFree(n->dbuf0);
+    cudaFree(n->dbuf1);
+    cudaFree(n->lossbuf);
+    cudaFree(n->param);
+    cudaFree(n->grad);
+    cudaFree(n->m1);
+    cudaFree(n->m2);
+    delete n;
+}
+
+int kd_mlp_num_params(kd_mlp* n, int64_t* count) {
+    if (!n || !count) return err(KD_ERR_ARG, "kd_mlp_num_params: null argument");
+    *count = (int64_t)n->nparam;
+    return KD_OK;
+}
+
+int kd_mlp_set_params(kd_mlp* n, const float* p, int32_t where) {
+    if (!n || !p) return err(KD_ERR_ARG, "kd_mlp_set_params: null argument");
+    MLP_CUDA(cudaSetDevice(n->device));
+    int rc = copy_io(n->param, p, n->nparam * sizeof(float), KD_DEVICE, where, 0);
+    if (rc) return rc;
+    MLP_CUDA(cudaMemset(n->m1, 0, n->nparam * sizeof(float)));
+    MLP_CUDA(cudaMemset(n->m2, 0, n->nparam * sizeof(float)));
+    n->adam_t = 0;
+    MLP_CUDA(cudaDeviceSynchronize());
+    return KD_OK;
+}
+
+int kd_mlp_get_params(kd_mlp* n, float* p, int32_t where) {
+    if (!n || !p) return err(KD_ERR_ARG, "kd_mlp_get_params: null argument");
+    MLP_CUDA(cudaSetDevice(n->device));
+    int rc = copy_io(p, n->param, n->nparam * sizeof(float), where, KD_DEVICE, 0);
+    if (rc) return rc;
+    MLP_CUDA(cudaDeviceSynchronize());
+    return KD_OK;
+}
+
+int kd_mlp_forward(kd_mlp* n, const float* x, int32_t batch, float* y, int32_t where, void* cuda_stream) {
+    if (!n || !x || !y || batch <= 0) return err(KD_ERR_ARG, "kd_mlp_forward: bad argument");
+    MLP_CUDA(cudaSetDevice(n->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int rc = ensure_cap(n, batch);
+    if (rc) return rc;
+    const float* xd = x;
+    if (where == KD_HOST) {
+        rc = copy_io(n->dbuf1, x, sizeof(float) * (size_t)batch * n->w[0], KD_DEVICE, KD_HOST, s);
+        if (rc) return rc;
+        xd = n->dbuf1;
+    }
+    rc = forward(n, xd, batch, s);
+    if (rc) return rc;
+    rc = copy_io(y, n->a[n->L], sizeof(float) * (size_t)batch * n->w[n->L], where, KD_DEVICE, s);
+    if (rc) return rc;
+    if (where == KD_HOST) MLP_CUDA(cudaStreamSynchronize(s));
+    return KD_OK;
+}
+
+int kd_mlp_gradients(kd_mlp* n, const float* x, const float* t, int32_t batch, float* loss,
+                     float* grads, int32_t where, void* cuda_stream) {
+    if (!n || !x || !t || batch <= 0) return err(KD_ERR_ARG, "kd_mlp_gradients: bad argument");
+    MLP_CUDA(cudaSetDevice(n->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int rc = ensure_cap(n, batch);
+    if (rc) return rc;
+    const float* xd = x;
+    const float* td = t;
+    float* tmp_x = nullptr;
+    float* tmp_t = nullptr;
+    if (where == KD_HOST) {  // staged through the gradient buffers' tail: copy to device scratch
+        MLP_CUDA(cudaMalloc(&tmp_x, sizeof(float) * (size_t)batch * n->w[0]));
+        MLP_CUDA(cudaMalloc(&tmp_t, sizeof(float) * (size_t)batch * n->w[n->L]));
+        rc = copy_io(tmp_x, x, sizeof(float) * (size_t)batch * n->w[0], KD_DEVICE, KD_HOST, s);
+        if (!rc) rc = copy_io(tmp_t, t, sizeof(float) * (size_t)batch * n->w[n->L], KD_DEVICE, KD_HOST, s);
+        if (rc) { cudaFree(tmp_x); cudaFree(tmp_t); return rc; }
+        xd = tmp_x;
+        td = tmp_t;
+    }
+    rc = forward(n, xd, batch, s);
+    if (!rc) rc = backward(n, td, batch, s);
+    if (!rc && loss) rc = copy_io(loss, n->lossbuf, sizeof(float), where, KD_DEVICE, s);
+    if (!rc && grads) rc = copy_io(grads, n->grad, n->nparam * sizeof(float), where, KD_DEVICE, s);
+    if (where == KD_HOST) cudaStreamSynchronize(s);
+    cudaFree(tmp_x);
+    cudaFree(tmp_t);
+    return rc;
+}
+
+int kd_mlp_train_step(kd_mlp* n, const float* x, const float* t, int32_t batch, float lr,
+                      float* loss_dev, void* cuda_stream) {
+    if (!n || !x || !t || batch <= 0 || !(lr > 0)) return err(KD_ERR_ARG, "kd_mlp_train_step: bad argument");
+    MLP_CUDA(cudaSetDevice(n->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int rc = ensure_cap(n, batch);
+    if (rc) return rc;
+    rc = forward(n, x, batch, s);
+    if (!rc) rc = backward(n, t, batch, s);
+    if (rc) return rc;
+    ++n->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)n->adam_t), c2 = 1.0f - powf(b2, (float)n->adam_t);
+    k_adam<<<(int)((n->nparam + 255) / 256), 256, 0, s>>>(n->param, n->grad, n->m1, n->m2, (long)n->nparam,
+                                                          lr, b1, b2, 1e-8f, c1, c2);
+    MLP_CUDA(cudaGetLastError());
+    if (loss_dev) MLP_CUDA(cudaMemcpyAsync(loss_dev, n->lossbuf, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return KD_OK;
+}
+
+}  // extern "C"

@@ -98,6 +98,14 @@ _SIGS = {
     "kd_batch_step": (C.c_int, [_vp, _P(C.c_double), C.c_int64, C.c_int64, _P(kd_obs), C.c_int64,
                                 _P(C.c_int64)]),
     "kd_batch_destroy": (None, [_vp]),
+    "kd_mlp_create": (C.c_int, [_P(C.c_int32), C.c_int32, _P(_vp)]),
+    "kd_mlp_num_params": (C.c_int, [_vp, _P(C.c_int64)]),
+    "kd_mlp_set_params": (C.c_int, [_vp, _vp, C.c_int32]),
+    "kd_mlp_get_params": (C.c_int, [_vp, _vp, C.c_int32]),
+    "kd_mlp_forward": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.c_int32, _vp]),
+    "kd_mlp_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, _vp, C.c_int32, _vp]),
+    "kd_mlp_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_float, _vp, _vp]),
+    "kd_mlp_destroy": (None, [_vp]),
     "kd_destroy": (None, [_vp]),
     "kd_last_error": (C.c_char_p, []),
     "kd_version": (C.c_int, []),
@@ -289,3 +297,59 @@ class Batch:
                              C.byref(got)))
         return [[{k: getattr(buf[i * nobs + j], k) for k in OBS_FIELDS} for j in range(nobs)]
                 for i in range(n)]
+
+
+class MLP:
+    """The surrogate network (``kd_mlp_*``): widths[0] -> ... -> widths[-1], GELU hidden."""
+
+    def __init__(self, widths):
+        self.widths = [int(w) for w in widths]
+        arr = (C.c_int32 * len(self.widths))(*self.widths)
+        h = _vp()
+        _check(kd_mlp_create(arr, len(self.widths) - 1, C.byref(h)))
+        self._h = h
+        n = C.c_int64()
+        _check(kd_mlp_num_params(h, C.byref(n)))
+        self.nparam = n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            kd_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, np.float32)
+        assert a.size == self.nparam
+        _check(kd_mlp_set_params(self._h, a.ctypes.data_as(_vp), KD_HOST))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.nparam, np.float32)
+        _check(kd_mlp_get_params(self._h, a.ctypes.data_as(_vp), KD_HOST))
+        return a
+
+    def forward(self, x) -> np.ndarray:
+        xa = np.ascontiguousarray(x, np.float32)
+        y = np.empty((xa.shape[0], self.widths[-1]), np.float32)
+        _check(kd_mlp_forward(self._h, xa.ctypes.data_as(_vp), xa.shape[0], y.ctypes.data_as(_vp),
+                              KD_HOST, None))
+        return y
+
+    def gradients(self, x, t):
+        xa = np.ascontiguousarray(x, np.float32)
+        ta = np.ascontiguousarray(t, np.float32)
+        g = np.empty(self.nparam, np.float32)
+        loss = np.empty(1, np.float32)
+        _check(kd_mlp_gradients(self._h, xa.ctypes.data_as(_vp), ta.ctypes.data_as(_vp), xa.shape[0],
+                                loss.ctypes.data_as(_vp), g.ctypes.data_as(_vp), KD_HOST, None))
+        return float(loss[0]), g
+
+    def train_step(self, x_dev, t_dev, batch: int, lr: float, loss_dev=None, stream=None):
+        """Device pointers (ints, e.g. torch data_ptr())."""
+        _check(kd_mlp_train_step(self._h, _vp(x_dev), _vp(t_dev), batch, lr,
+                                 _vp(loss_dev) if loss_dev else None, _vp(stream) if stream else None))
