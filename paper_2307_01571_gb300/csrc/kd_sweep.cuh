@@ -582,7 +582,13 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
         c.valid = c.line < (AXIS == AXIS_X ? a.ny : a.nx);
         c.sm = reinterpret_cast<U*>(smem_raw);
         C v[E * NC];
+        // programmatic dependent launch: everything above ran while the previous kernel
+        // in the stream was still finishing; its results are visible after this wait
+        // (a hardware-managed wait for the prerequisite grid, not a spin loop)
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         load<LR_LOAD>(a, c, v);
+        // the next kernel may start its own prologue as our CTAs retire
+        asm volatile("griddepcontrol.launch_dependents;");
         if constexpr (AXIS == AXIS_Y) {
             C kab[E];
             if (a.op == OP_KINETIC) load_ktab(a, c, kab);
@@ -615,9 +621,17 @@ cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
         attr_done = true;
     }
     const int lines = AXIS == AXIS_X ? a.ny : a.nx;
-    dim3 grid(((lines + Cf::BATCH - 1) / Cf::BATCH) * Cf::NPAIRS);
-    k<<<grid, Cf::THREADS, Cf::SMEM_BYTES, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(((lines + Cf::BATCH - 1) / Cf::BATCH) * Cf::NPAIRS);
+    cfg.blockDim = dim3(Cf::THREADS);
+    cfg.dynamicSmemBytes = Cf::SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, a);
 }
 
 // Fills the stage-major twiddle table of an N = 2^LOGN sweep in FP64 (sincospi):

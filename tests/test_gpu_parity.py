@@ -240,3 +240,50 @@ def test_device_pointers_and_torch_stream(kd):
             sim.get_spinor(out)
             s.synchronize()
     assert rel(out.cpu().numpy(), ref) <= 1e-10
+
+
+def test_2048x1024_precision_form_against_oracle(kd):
+    """BASELINE config 3's grid (FP32 bulk, FP64-built tables) element by element against
+    the oracle over 3 steps."""
+    wl = W.c3(precision=1, nsteps=3)
+    u, g, f, pk = wl.units, wl.grid, wl.field, wl.packet
+    ref = oracle.init_packet(u, g, f, pk)
+    ref = oracle.step(u, g, f, ref, 0.0, wl.dt, 3)
+    with kd.Sim.from_workload(wl) as sim:
+        sim.init_packet(pk)
+        sim.step(wl.dt, 3)
+        got = sim.get_spinor()
+    assert rel(got, ref) <= TOL[1]
+
+
+@pytest.mark.parametrize("prec,n", [(1, 4096), (0, 2048)])
+def test_largest_grids_free_plane_wave_is_exact(kd, prec, n):
+    """At the largest supported sizes (oracle out of reach): a positive-energy plane wave
+    u^+(pi) e^{i p.x} is an eigenstate of every factor of the step, so after N steps the
+    state is the initial one times exp(-i (E - v p_y) N dt / hbar), computed here on the
+    host from the oracle's bispinor."""
+    u = W.NATURAL
+    g = W.Grid(n, n, -float(n), float(n), -float(n), float(n))
+    f = W.Field(kind=W.NONE, p_shift_y=1.0, box_vy=0.5)
+    kx, ky = 7, n - 3
+    pix, piy = oracle.momentum(g, u, f, kx, ky)
+    px, py = pix, piy - 1.0
+    us = oracle.spinor_u(u, pix, piy, 1, 0)
+    x = g.x_min + np.arange(n) * (g.x_max - g.x_min) / n
+    y = g.y_min + np.arange(n) * (g.y_max - g.y_min) / n
+    ph_x = np.exp(1j * px * (x - g.x_min))
+    ph_y = np.exp(1j * py * (y - g.y_min))
+    psi0 = (ph_y[:, None, None] * ph_x[None, :, None]) * us[None, None, :]
+    steps, dt = 50, 0.05
+    E = math.sqrt(1.0 + pix * pix + piy * piy)
+    ref_phase = np.exp(-1j * (E - 0.5 * py) * steps * dt)
+    with kd.Sim(u, g, f, prec) as sim:
+        sim.set_spinor(psi0)
+        sim.step(dt, steps)
+        got = sim.get_spinor()
+    del psi0
+    # compare on a strided sample of rows (the whole array at 4096^2 is 512 MiB complex128)
+    rows = np.arange(0, n, 97)
+    exp = (ph_y[rows, None, None] * ph_x[None, :, None]) * us[None, None, :] * ref_phase
+    err = np.max(np.abs(got[rows] - exp))
+    assert err <= (1e-10 if prec == 0 else 2e-4), err
