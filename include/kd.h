@@ -190,7 +190,7 @@ int kd_batch_step(kd_batch* batch, const double* dt, int64_t nsteps, int64_t obs
                   kd_obs* obs_out, int64_t obs_cap, int64_t* n_obs);
 void kd_batch_destroy(kd_batch* batch);
 
-/* Surrogate network (BASELINE's learned part; the paper has no network): a fully
+/* Surrogate network (a learned stand-in for the solver's read-outs; the paper has no network): a fully
  * connected MLP, widths[0] inputs -> ... -> widths[nlayers] outputs, exact-erf GELU on the
  * hidden layers, linear output, trained with mean squared error and Adam
  * (beta = 0.9, 0.999, eps = 1e-8) by hand-written FP32 kernels; every reduction runs in a

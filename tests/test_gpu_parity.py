@@ -243,8 +243,8 @@ def test_device_pointers_and_torch_stream(kd):
 
 
 def test_2048x1024_precision_form_against_oracle(kd):
-    """BASELINE config 3's grid (FP32 bulk, FP64-built tables) element by element against
-    the oracle over 3 steps."""
+    """The 2048x1024 grid over an 80 lambda x-box (FP32 arithmetic, FP64-built tables)
+    element by element against the oracle over 3 steps."""
     wl = W.c3(precision=1, nsteps=3)
     u, g, f, pk = wl.units, wl.grid, wl.field, wl.packet
     ref = oracle.init_packet(u, g, f, pk)
