@@ -199,10 +199,13 @@ def batched_form(kd, stream, K, barrier, dist):
     members = W.c4()
     pts = sum(w.points for w in members) * members[0].nsteps
     sims = [kd.Sim.from_workload(w, stream=stream.cuda_stream) for w in members]
+    chosen = {}
     for s_, w in zip(sims, members):
         s_.init_packet(w.packet)
+        # launch variants per grid shape (timed once per shape, then looked up)
+        chosen[f"{w.grid.nx}x{w.grid.ny}"] = s_.autotune(w.dt, reps=50)["variants"]
     dts = [w.dt for w in members]
-    res = {}
+    res = {"sweep_variants": chosen}
     with kd.Batch(sims, stream=stream.cuda_stream) as b:
         b.step(dts, members[0].nsteps, obs_every=100)           # warm-up: graphs captured
         barrier()
@@ -290,6 +293,7 @@ def main():
         wl = W.c2(precision=prec, nsteps=args.strang)
         sim = kd.Sim.from_workload(wl, stream=stream.cuda_stream)
         sim.init_packet(wl.packet)
+        tune = sim.autotune(wl.dt, reps=50)    # launch variants of both sweeps (untimed)
         n0 = sim.observe()["norm"]
         for _ in range(Wm):
             sim.step(wl.dt, wl.nsteps, obs_every=wl.obs_every)
@@ -323,12 +327,13 @@ def main():
             e1.synchronize()
             sweep_ms[name] = e0.elapsed_time(e1) / reps
         sim.close()
-        return wl, ms, launches, ck_res, drift, sweep_ms
+        return wl, ms, launches, ck_res, drift, sweep_ms, tune
 
     def e2e_form(prec: int, K: int):
         wl = W.c2(precision=prec, nsteps=args.strang)
         sim = kd.Sim.from_workload(wl, stream=stream.cuda_stream)
         sim.init_packet(wl.packet)
+        sim.autotune(wl.dt)                               # the recorded choice (no timing)
         host_in = torch.from_numpy(sim.get_spinor()).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         sim.step(wl.dt, wl.nsteps, obs_every=wl.obs_every)
@@ -370,7 +375,7 @@ def main():
                 "launch_ms": {k: round(v, 5) for k, v in sweep_ms.items()}}
 
     K, Wm = args.steps, max(3, args.warmup)
-    wl, ms, launches, clk, drift, sweep_ms = timed_form(W.FP32, K, Wm, True)
+    wl, ms, launches, clk, drift, sweep_ms, tune = timed_form(W.FP32, K, Wm, True)
     pts = wl.points * wl.nsteps * K * world
     value = pts / (ms * 1e-3)
     line = {
@@ -381,7 +386,10 @@ def main():
                    "strang_steps_per_step": wl.nsteps, "obs_every": wl.obs_every,
                    "l2": "flushed between timed steps (256 MiB write); the 20 MiB spinor and "
                          "tables stay L2-resident inside a step",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "sweep_variants": {"chosen": tune["variants"],
+                                      "us_per_launch": {k: [round(1e3 * m, 2) for m in v]
+                                                        for k, v in tune["ms"].items()}}},
         "roofline": roofline("fp32", wl, sweep_ms, hbm),
         "gpu_launches": launches,
         "clocks": clk,
@@ -392,7 +400,7 @@ def main():
                    "d2h_bytes_per_step": bo}
     if not args.no_fp64:
         K64 = max(1, min(K, 3))
-        wl64, ms64, l64, _, drift64, sw64 = timed_form(W.FP64, K64, 3, False)
+        wl64, ms64, l64, _, drift64, sw64, _ = timed_form(W.FP64, K64, 3, False)
         v64 = wl64.points * wl64.nsteps * K64 * world / (ms64 * 1e-3)
         line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
                         "norm_drift": drift64, "speedup_fp32_over_fp64": value / v64,

@@ -222,6 +222,32 @@ void kd_mlp_destroy(kd_mlp* net);
  * The launches of one (kind, reps) pair are captured once into a CUDA graph and replayed. */
 int kd_bench_sweep(kd_sim* sim, int32_t kind, int32_t reps);
 
+/* FFT autotuner.  The FP32 sweeps are compiled in KD_SWEEP_VARIANTS launch variants
+ * per axis, differing in radix schedule (radix-8 or radix-4 Stockham stages of the 2D
+ * FFT of Sec. II.D), threads per CTA, column-tile width and spinor components per CTA.
+ * Variant 0 is the default.  kd_autotune times every variant of both sweeps on this
+ * simulation's grid (reps back-to-back launches each, graph-replayed, reading the state
+ * and writing only scratch: the state is unchanged) with the step's pointwise ops for
+ * time step dt, keeps variant 0 unless another is faster by more than 2 %, and applies
+ * the choice to this simulation.  The choice is remembered for the process per device,
+ * grid and field kind, so later simulations of that shape only look it up (flags =
+ * KD_TUNE_FORCE times again).  variant_x / variant_y (may be NULL) receive the choice,
+ * times_ms (may be NULL, 2 * KD_SWEEP_VARIANTS floats: x then y) the measured ms per
+ * launch (the recorded ones when the choice was looked up; -1 for FP64).  FP64
+ * simulations have one variant (0).  Synchronises the simulation's stream; must not be called while the
+ * stream is being captured.  Variants 0 and 1 differ only in threads per CTA and give
+ * bitwise identical results; the radix-4 schedule (2) and the components-per-CTA change
+ * (3) round differently in the last bits (every variant meets the same accuracy).  A
+ * simulation's results are reproducible for fixed variants.  kd_set_sweep_variants selects variants directly
+ * (KD_ERR_ARG out of range), kd_get_sweep_variants reads them back.  The variants are
+ * not part of a kd_get_state checkpoint. */
+#define KD_SWEEP_VARIANTS 4
+#define KD_TUNE_FORCE 1
+int kd_autotune(kd_sim* sim, double dt, int32_t reps, int32_t flags, int32_t* variant_x,
+                int32_t* variant_y, float* times_ms);
+int kd_set_sweep_variants(kd_sim* sim, int32_t variant_x, int32_t variant_y);
+int kd_get_sweep_variants(kd_sim* sim, int32_t* variant_x, int32_t* variant_y);
+
 /* Number of kernel launches this simulation has enqueued so far (graph replays counted
  * node by node). */
 int kd_get_launch_count(kd_sim* sim, int64_t* launches);

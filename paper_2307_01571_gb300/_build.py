@@ -1,7 +1,8 @@
 """Compiles the CUDA library ``libkd.so`` in-tree for sm_103a.
 
-The three translation units (host API, FP32 sweeps, FP64 sweeps) compile in parallel
-with nvcc; the CUDA runtime is linked statically so the library only needs the driver.
+The translation units (host API, the FP32 sweeps once per launch variant, the FP64
+sweeps, the allocation-free entry and the MLP kernels) compile in parallel with nvcc; the
+CUDA runtime is linked statically so the library only needs the driver.
 """
 from __future__ import annotations
 
@@ -15,7 +16,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkd.so")
-SOURCES = ["kd_api.cu", "kd_sweep_f32.cu", "kd_sweep_f64.cu", "kd_noalloc.cu", "kd_mlp.cu"]
+SWEEP_VARIANTS = 4    # KD_SWEEP_VARIANTS in csrc/kd_internal.h
+# (source, object, extra defines)
+UNITS = ([("kd_api.cu", "kd_api.o", [])]
+         + [("kd_sweep_f32.cu", f"kd_sweep_f32_v{v}.o", [f"-DKD_SWEEP_VARIANT={v}"])
+            for v in range(SWEEP_VARIANTS)]
+         + [("kd_sweep_f64.cu", "kd_sweep_f64.o", []), ("kd_noalloc.cu", "kd_noalloc.o", []),
+            ("kd_mlp.cu", "kd_mlp.o", [])])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{os.path.join(ROOT, 'include')}"]
@@ -47,9 +54,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, obj, defs = unit
+        obj = os.path.join(BUILD, obj)
+        cmd = [nvcc, *ARCH, *FLAGS, *defs, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -57,8 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(len(UNITS)) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -22,6 +23,8 @@
 #include "kd_internal.h"
 
 using namespace kd;
+
+static_assert(KD_SWEEP_VARIANTS == kNumSweepVariants, "public and internal variant counts");
 
 namespace {
 
@@ -83,8 +86,8 @@ struct kd_sim {
     size_t P;
     void* psi = nullptr;
     void* work = nullptr;
-    void* tw_x = nullptr;
-    void* tw_y = nullptr;
+    void* tw[2][2] = {};   // twiddle tables [axis][loge - 2] (radix-4 and radix-8 schedules)
+    int var[2] = {0, 0};   // sweep launch variant per axis (kd_autotune)
     void* xtab = nullptr;
     void* kxtab = nullptr;
     void* kytab = nullptr;
@@ -503,16 +506,18 @@ __global__ void k_permute(const T* in, T* out, size_t npts, int to_internal) {
 int grid_blocks(size_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
 template <typename T> int upload_tables_t(kd_sim* s) {
-    const int nx = s->g.nx, ny = s->g.ny;
+    const int nx = s->g.nx;
     // stage-major twiddle tables, built on the device in FP64 (<= 2N entries of 16 B)
-    for (int ax = 0; ax < 2; ++ax) {
-        int entries = 0;
-        const int logn = ax == 0 ? s->lx : s->ly;
-        void* dst = ax == 0 ? s->tw_x : s->tw_y;
-        KD_CUDA(sizeof(T) == 4 ? build_twiddles_f32(logn, dst, &entries, s->stream)
-                               : build_twiddles_f64(logn, dst, &entries, s->stream));
-        if (entries > 2 * (1 << logn)) return fail(KD_ERR_CUDA, "twiddle table overflow");
-    }
+    // for both radix schedules a launch variant may use
+    for (int ax = 0; ax < 2; ++ax)
+        for (int le = 2; le <= 3; ++le) {
+            int entries = 0;
+            const int logn = ax == 0 ? s->lx : s->ly;
+            void* dst = s->tw[ax][le - 2];
+            KD_CUDA(sizeof(T) == 4 ? build_twiddles_f32(logn, le, dst, &entries, s->stream)
+                                   : build_twiddles_f64(logn, le, dst, &entries, s->stream));
+            if (entries > 2 * (1 << logn)) return fail(KD_ERR_CUDA, "twiddle table overflow");
+        }
     // per-x field table (Eqs. Equation_of_Gaussian_beam, Phase_of_Gaussian_beam and w(x)),
     // two 4-vectors per column stored as [2][nx]: (Theta0 = (-k x + zeta) mod 2 pi,
     // x/(x_R w^2), w0/w, 1/w^2) and (1/w, cos zeta, sin zeta, cos k x), zeta = atan(x/x_R)
@@ -609,7 +614,9 @@ cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* 
     a.nx = s->g.nx;
     a.ny = s->g.ny;
     a.op = op;
-    a.tw = axis == AXIS_X ? s->tw_x : s->tw_y;
+    const int logn = axis == AXIS_X ? s->lx : s->ly;
+    const int var = s->prec == KD_FP64 ? 0 : s->var[axis];
+    a.tw = s->tw[axis][sweep_loge(s->prec == KD_FP64, axis, logn, var) - 2];
     a.clock = s->clock;
     a.steps = s->steps;
     a.n_local = n_local;
@@ -630,10 +637,86 @@ cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* 
     a.mc_f = (float)a.mc;
     a.invP = 1.0 / ((double)s->g.nx * (double)s->g.ny);
     a.invP_f = (float)a.invP;
-    const int logn = axis == AXIS_X ? s->lx : s->ly;
     ++s->launches;
     return s->prec == KD_FP64 ? launch_sweep_f64(axis, shape, logn, a, s->stream)
-                              : launch_sweep_f32(axis, shape, logn, a, s->stream);
+                              : launch_sweep_f32(var, axis, shape, logn, a, s->stream);
+}
+
+// ------------------------------------------------------------------ autotuner ------
+// Process-wide record of tuned launch variants per device, grid and field kind, so that
+// simulations of the same shape (the members of a batch, repeated runs) are timed once.
+struct TuneKey {
+    int device, nx, ny, kind, longitudinal;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(device, nx, ny, kind, longitudinal) <
+               std::tie(o.device, o.nx, o.ny, o.kind, o.longitudinal);
+    }
+};
+struct TuneResult {
+    int var[2];
+    float ms[2][KD_SWEEP_VARIANTS];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneResult> g_tune;
+
+// First launch of every sweep shape of the current variants outside any stream capture
+// (sets the kernels' shared-memory attributes); reads psi, writes only the work buffer.
+int warm_variants(kd_sim* s) {
+    const int shapes[3] = {SHAPE_F1, SHAPE_F2, SHAPE_F1F2};
+    for (int ax = 0; ax < 2; ++ax)
+        for (int sh : shapes) {
+            cudaError_t el = sweep(s, ax, sh, OP_NONE, s->psi, s->work, 0, 0.0);
+            if (el != cudaSuccess) return fail(KD_ERR_CUDA, "sweep launch: %s", cudaGetErrorString(el));
+        }
+    KD_CUDA(cudaStreamSynchronize(s->stream));
+    return KD_OK;
+}
+
+// Mean time per launch (ms) of `reps` back-to-back full sweeps of one axis with the
+// step's pointwise op, psi -> work (the state is not modified).  The launches are
+// captured into a graph and replayed twice after one warm replay, so that host launch
+// overhead does not enter.
+int time_sweep(kd_sim* s, int axis, int reps, double dt, float* ms) {
+    cudaStream_t user = s->stream;
+    s->stream = s->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        s->stream = user;
+        return fail(KD_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    }
+    cudaError_t el = cudaSuccess;
+    for (int i = 0; i < reps && el == cudaSuccess; ++i)
+        el = axis == AXIS_X ? sweep(s, AXIS_X, SHAPE_F1F2, OP_POTENTIAL, s->psi, s->work, 0, dt)
+                            : sweep(s, AXIS_Y, SHAPE_F1F2, OP_KINETIC, s->psi, s->work, 0, 0.0);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s->stream, &graph);
+    s->stream = user;
+    if (el != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(KD_ERR_CUDA, "tuning capture: %s", cudaGetErrorString(el != cudaSuccess ? el : e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(KD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int rc = KD_OK;
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess ||
+        cudaGraphLaunch(exec, s->stream) != cudaSuccess ||
+        cudaEventRecord(ev[0], s->stream) != cudaSuccess ||
+        cudaGraphLaunch(exec, s->stream) != cudaSuccess ||
+        cudaGraphLaunch(exec, s->stream) != cudaSuccess ||
+        cudaEventRecord(ev[1], s->stream) != cudaSuccess ||
+        cudaEventSynchronize(ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(ms, ev[0], ev[1]) != cudaSuccess)
+        rc = fail(KD_ERR_CUDA, "tuning run failed: %s", cudaGetErrorString(cudaGetLastError()));
+    else
+        *ms /= (float)(2 * reps);
+    s->launches += 2 * (int64_t)reps;   // replays beyond the one counted at capture
+    for (cudaEvent_t v : ev)
+        if (v) cudaEventDestroy(v);
+    cudaGraphExecDestroy(exec);
+    return rc;
 }
 
 #define KD_LAUNCH(expr)                                                                  \
@@ -952,8 +1035,10 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
         return bail(fail(KD_ERR_CUDA, "stream create failed"));
     KD_ALLOC(s->psi, spinor_bytes(s));
     KD_ALLOC(s->work, spinor_bytes(s));
-    KD_ALLOC(s->tw_x, 2 * (size_t)grid->nx * 16);
-    KD_ALLOC(s->tw_y, 2 * (size_t)grid->ny * 16);
+    for (int le = 0; le < 2; ++le) {
+        KD_ALLOC(s->tw[AXIS_X][le], 2 * (size_t)grid->nx * 16);
+        KD_ALLOC(s->tw[AXIS_Y][le], 2 * (size_t)grid->ny * 16);
+    }
     KD_ALLOC(s->xtab, 8 * (size_t)grid->nx * s->tsize);
     KD_ALLOC(s->kxtab, (size_t)grid->nx * s->tsize);
     KD_ALLOC(s->kytab, 4 * (size_t)grid->ny * s->tsize);
@@ -970,15 +1055,8 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
         return bail(fail(KD_ERR_CUDA, "memset failed"));
     int rc = precision == KD_FP64 ? upload_tables_t<double>(s) : upload_tables_t<float>(s);
     if (rc) return bail(rc);
-    // first launch of every sweep shape outside any stream capture (sets kernel
-    // attributes); the spinor is zero, so this leaves it unchanged
-    const int shapes[3] = {SHAPE_F1, SHAPE_F2, SHAPE_F1F2};
-    for (int ax = 0; ax < 2; ++ax)
-        for (int sh : shapes) {
-            cudaError_t el = sweep(s, ax, sh, OP_NONE, s->psi, s->psi, 0, 0.0);
-            if (el != cudaSuccess) return bail(fail(KD_ERR_CUDA, "sweep launch: %s", cudaGetErrorString(el)));
-        }
-    if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(KD_ERR_CUDA, "device synchronize failed"));
+    rc = warm_variants(s);
+    if (rc) return bail(rc);
     *out = s;
     return KD_OK;
 }
@@ -988,8 +1066,9 @@ void kd_destroy(kd_sim* s) {
     cudaSetDevice(s->device);
     cudaStreamSynchronize(s->stream);
     clear_graphs(s);
-    void* bufs[] = {s->psi, s->work, s->tw_x, s->tw_y, s->xtab, s->kxtab, s->kytab, s->ktab,
-                    s->clock, s->steps, s->rowsum, s->md, s->scalar, s->obs_dev, s->status};
+    void* bufs[] = {s->psi, s->work, s->tw[0][0], s->tw[0][1], s->tw[1][0], s->tw[1][1], s->xtab,
+                    s->kxtab, s->kytab, s->ktab, s->clock, s->steps, s->rowsum, s->md, s->scalar,
+                    s->obs_dev, s->status};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -1508,6 +1587,97 @@ int kd_bench_sweep(kd_sim* s, int32_t kind, int32_t reps) {
     }
     KD_CUDA(cudaGraphLaunch(it->second.first, s->stream));
     s->launches += it->second.second;
+    return KD_OK;
+}
+
+int kd_set_sweep_variants(kd_sim* s, int32_t variant_x, int32_t variant_y) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    const int nv = s->prec == KD_FP64 ? 1 : KD_SWEEP_VARIANTS;
+    if (variant_x < 0 || variant_x >= nv || variant_y < 0 || variant_y >= nv)
+        return fail(KD_ERR_ARG, "sweep variant out of range [0, %d)", nv);
+    if (s->var[0] == variant_x && s->var[1] == variant_y) return KD_OK;
+    s->var[0] = variant_x;
+    s->var[1] = variant_y;
+    clear_graphs(s);
+    return warm_variants(s);
+}
+
+int kd_get_sweep_variants(kd_sim* s, int32_t* variant_x, int32_t* variant_y) {
+    if (!s || !variant_x || !variant_y) return fail(KD_ERR_ARG, "null argument");
+    *variant_x = s->var[0];
+    *variant_y = s->var[1];
+    return KD_OK;
+}
+
+int kd_autotune(kd_sim* s, double dt, int32_t reps, int32_t flags, int32_t* variant_x,
+                int32_t* variant_y, float* times_ms) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!(dt > 0) || !isfinite(dt)) return fail(KD_ERR_ARG, "dt must be positive and finite");
+    if (reps < 1 || reps > 4096) return fail(KD_ERR_ARG, "reps must be in [1, 4096]");
+    if (flags & ~KD_TUNE_FORCE) return fail(KD_ERR_ARG, "unknown flags");
+    TuneResult res{};
+    for (auto& a : res.ms)
+        for (float& m : a) m = -1.0f;
+    if (s->prec == KD_FP64) {   // one compiled variant: nothing to choose
+        rc = kd_set_sweep_variants(s, 0, 0);
+        if (rc) return rc;
+    } else {
+        const TuneKey key{s->device, s->g.nx, s->g.ny, s->f.kind, s->f.longitudinal};
+        bool cached = false;
+        if (!(flags & KD_TUNE_FORCE)) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) { res = it->second; cached = true; }
+        }
+        if (!cached) {
+            // the step's tables and one step's scalars for dt at the current time
+            if (dt != s->ktab_dt) {
+                rc = build_dt_tables(s, dt);
+                if (rc) return rc;
+                clear_graphs(s);
+            }
+            rc = ensure_steps(s, 1);
+            if (rc) return rc;
+            const double omega = s->u.c * s->f.k_L;
+            k_step_scalars<<<1, 256, 0, s->stream>>>(s->steps, 1, s->t0 + (double)s->step * s->dt_clock, 0,
+                                                     dt, s->f.a0, omega, s->f.phase0, s->f.env_T,
+                                                     s->f.box_vy, s->g.y_min);
+            KD_CUDA(cudaGetLastError());
+            k_set_clock<<<1, 1, 0, s->stream>>>(s->clock, 0);
+            KD_CUDA(cudaGetLastError());
+            s->launches += 2;
+            const int keep[2] = {s->var[0], s->var[1]};
+            for (int ax = 0; ax < 2 && !rc; ++ax) {
+                for (int v = 0; v < KD_SWEEP_VARIANTS && !rc; ++v) {
+                    s->var[ax] = v;
+                    rc = warm_variants(s);
+                    if (!rc) rc = time_sweep(s, ax, reps, dt, &res.ms[ax][v]);
+                }
+                // the default stays unless another variant is faster by more than 2 %
+                int best = 0;
+                for (int v = 1; v < KD_SWEEP_VARIANTS; ++v)
+                    if (res.ms[ax][v] < 0.98f * res.ms[ax][best]) best = v;
+                res.var[ax] = best;
+                s->var[ax] = keep[ax];
+            }
+            if (rc) {
+                s->var[0] = keep[0];
+                s->var[1] = keep[1];
+                return rc;
+            }
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = res;
+        }
+        rc = kd_set_sweep_variants(s, res.var[0], res.var[1]);
+        if (rc) return rc;
+    }
+    if (variant_x) *variant_x = s->var[0];
+    if (variant_y) *variant_y = s->var[1];
+    if (times_ms)
+        for (int ax = 0; ax < 2; ++ax)
+            for (int v = 0; v < KD_SWEEP_VARIANTS; ++v) times_ms[ax * KD_SWEEP_VARIANTS + v] = res.ms[ax][v];
     return KD_OK;
 }
 

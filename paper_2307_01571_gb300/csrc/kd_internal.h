@@ -65,12 +65,52 @@ struct SweepArgs {
     double mc;            // m c
 };
 
-// Launches one sweep; returns cudaSuccess or the launch error.  logn in [2, 12].
-cudaError_t launch_sweep_f32(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
+// Launch variants of the FP32 sweeps, timed per grid by the autotuner (kd_autotune);
+// variant 0 is the default.  A variant fixes the radix schedule (loge = log2 of the
+// elements a thread owns: radix-8 or radix-4 Stockham stages), the threads per CTA (a
+// target: at least one whole line), the minimum column-tile width of the y sweep, the
+// spinor components per CTA (2: one 2x2 pair per CTA, the two pairs' CTAs side by side;
+// 4: both pairs, sharing the field or table loads) and the resident warps per SM the
+// register budget is built for.  Variants that differ only in threads or tile width do
+// the same arithmetic per line (bitwise identical results); a different radix schedule,
+// or components per CTA (the compiler may fuse the pointwise ops' multiply-adds
+// differently), rounds differently.  FP64 sweeps have the one variant 0.
+struct SweepVariant {
+    int loge, threads, minb, nc, resident_warps;
+};
+constexpr int kNumSweepVariants = 4;
+__host__ __device__ constexpr SweepVariant sweep_variant(int axis, int v) {
+    return axis == AXIS_X
+        ? (v == 1 ? SweepVariant{3, 256, 1, 2, 24}
+         : v == 2 ? SweepVariant{2, 128, 1, 2, 32}
+         : v == 3 ? SweepVariant{3, 128, 1, 4, 16}
+                  : SweepVariant{3, 128, 1, 2, 28})
+        : (v == 1 ? SweepVariant{3, 512, 8, 4, 16}
+         : v == 2 ? SweepVariant{2, 256, 4, 4, 24}
+         : v == 3 ? SweepVariant{3, 256, 4, 2, 28}
+                  : SweepVariant{3, 256, 4, 4, 16});
+}
+// spinor components per CTA: FP64 CTAs own both pairs (the costly FP64 field is evaluated
+// once) except at N = 4096, where registers allow one pair
+__host__ __device__ constexpr int sweep_nc(bool f64, int axis, int logn, int v) {
+    return f64 ? (logn >= 12 ? 2 : 4) : sweep_variant(axis, v).nc;
+}
+// log2 of the elements per thread (the radix of the Stockham stages)
+__host__ __device__ constexpr int sweep_loge(bool f64, int axis, int logn, int v) {
+    const int lmax = f64 ? (sweep_nc(f64, axis, logn, v) == 2 ? 3 : 2) : sweep_variant(axis, v).loge;
+    return logn < lmax ? logn : lmax;
+}
+
+// Launches one sweep; returns cudaSuccess or the launch error.  logn in [2, 12],
+// variant in [0, kNumSweepVariants).
+template <int V>
+cudaError_t launch_sweep_f32_v(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_f32(int variant, int axis, int shape, int logn, const SweepArgs& a,
+                             cudaStream_t s);
 cudaError_t launch_sweep_f64(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
-// Fills the stage-major twiddle table of an N = 2^logn sweep (at most 2N entries of 16 B)
-// and returns the number of entries.
-cudaError_t build_twiddles_f32(int logn, void* out, int* entries, cudaStream_t s);
-cudaError_t build_twiddles_f64(int logn, void* out, int* entries, cudaStream_t s);
+// Fills the stage-major twiddle table of an N = 2^logn sweep whose threads own 2^loge
+// elements (at most 2N entries of 16 B) and returns the number of entries.
+cudaError_t build_twiddles_f32(int logn, int loge, void* out, int* entries, cudaStream_t s);
+cudaError_t build_twiddles_f64(int logn, int loge, void* out, int* entries, cudaStream_t s);
 
 }  // namespace kd

@@ -25,33 +25,6 @@
 
 #include "kd_internal.h"
 
-// Launch shape of the FP32 sweeps (compile-time; the defaults are the measured best on
-// GB300 for the 1024x512 grid): spinor components per CTA (2: one 2x2 pair, the CTAs of
-// the two pairs run side by side; 4: both pairs share field/table loads), threads per row
-// CTA, threads per column-tile CTA, the minimum column-tile width, and the resident warps
-// per SM the register budget targets.
-#ifndef KD_X_THREADS
-#define KD_X_THREADS 128
-#endif
-#ifndef KD_Y_THREADS
-#define KD_Y_THREADS 256
-#endif
-#ifndef KD_Y_MINB
-#define KD_Y_MINB 4
-#endif
-#ifndef KD_NC_X
-#define KD_NC_X 2
-#endif
-#ifndef KD_NC_Y
-#define KD_NC_Y 4
-#endif
-#ifndef KD_RESIDENT_WARPS_X
-#define KD_RESIDENT_WARPS_X 28
-#endif
-#ifndef KD_RESIDENT_WARPS_Y
-#define KD_RESIDENT_WARPS_Y 16
-#endif
-
 namespace kd {
 
 #define KD_DI __device__ __forceinline__
@@ -175,23 +148,21 @@ __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
 
-template <typename T, int LOGN, int AXIS> struct Cfg {
+template <typename T, int LOGN, int AXIS, int V> struct Cfg {
     static constexpr bool F64 = sizeof(T) == 8;
+    static constexpr SweepVariant VS = sweep_variant(AXIS, F64 ? 0 : V);
     static constexpr int N = 1 << LOGN;
-    // components per CTA: FP32 CTAs own one 2x2 pair (twice the resident warps at half
-    // the registers); FP64 CTAs own both pairs so the costly FP64 field is evaluated once
-    static constexpr int NC = F64 ? (LOGN >= 12 ? 2 : 4) : (AXIS == AXIS_X ? KD_NC_X : KD_NC_Y);
-    static constexpr int LOGRMAX = F64 ? (NC == 2 ? 3 : 2) : 3;
-    static constexpr int LOGE = LOGN < LOGRMAX ? LOGN : LOGRMAX;
+    static constexpr int NC = sweep_nc(F64, AXIS, LOGN, V);    // components per CTA
+    static constexpr int LOGE = sweep_loge(F64, AXIS, LOGN, V);
     static constexpr int E = 1 << LOGE;                          // elements per thread
     static constexpr int TF = N / E;                             // threads per line
-    // lines per CTA: rows are batched up to KD_X_THREADS threads; column tiles take
-    // KD_Y_THREADS threads and at least KD_Y_MINB (FP32) or 2 (FP64) columns, i.e.
-    // >= 64-128 contiguous bytes per tile row, within 512 threads
-    static constexpr int MINB = F64 ? 2 : KD_Y_MINB;
-    static constexpr int BATCH = AXIS == AXIS_X ? cmax(1, (F64 ? 128 : KD_X_THREADS) / TF)
+    // lines per CTA: rows are batched up to the variant's thread count; column tiles take
+    // that many threads and at least MINB columns (FP64: 2), i.e. >= 64-128 contiguous
+    // bytes per tile row, within 512 threads
+    static constexpr int MINB = F64 ? 2 : VS.minb;
+    static constexpr int BATCH = AXIS == AXIS_X ? cmax(1, (F64 ? 128 : VS.threads) / TF)
                                                 : (TF * MINB > 512 ? cmax(1, 512 / TF)
-                                                                   : cmax(MINB, (F64 ? 256 : KD_Y_THREADS) / TF));
+                                                                   : cmax(MINB, (F64 ? 256 : VS.threads) / TF));
     static constexpr int THREADS = TF * BATCH;
     static constexpr int CPP = F64 ? 1 : 2;                      // complex per 16-byte unit
     static constexpr int NPL = NC / CPP;                         // units per point in the CTA
@@ -199,10 +170,10 @@ template <typename T, int LOGN, int AXIS> struct Cfg {
     static constexpr int NPAIRS = 4 / NC;
     static constexpr int NST = plan_nst(LOGN, LOGE);
     static constexpr int BUF_UNITS = BATCH * NPL * N;            // one exchange buffer
-    // resident CTAs per SM the FP32 sweeps are built for (KD_RESIDENT_WARPS warps, so the
-    // 1024x512 grid's lines fit in one wave); FP64 sweeps keep their full register budget
-    static constexpr int MINBLK =
-        F64 ? 1 : cmax(1, (AXIS == AXIS_X ? KD_RESIDENT_WARPS_X : KD_RESIDENT_WARPS_Y) * 32 / THREADS);
+    // resident CTAs per SM the FP32 sweeps are built for (the variant's resident warps;
+    // the default puts the 1024x512 grid's lines in one wave); FP64 sweeps keep their full
+    // register budget
+    static constexpr int MINBLK = F64 ? 1 : cmax(1, VS.resident_warps * 32 / THREADS);
     // two exchange buffers (one barrier per exchange) only when they keep that occupancy
     static constexpr bool DB = 2 * BUF_UNITS * 16 * MINBLK <= 200 * 1024;
     static constexpr int SMEM_BYTES = NST > 1 ? (DB ? 2 : 1) * BUF_UNITS * 16 : 16;
@@ -246,8 +217,8 @@ template <> struct Unit<double> {
 };
 
 // ------------------------------------------------------------- the kernel ---------
-template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
-    using Cf = Cfg<T, LOGN, AXIS>;
+template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
+    using Cf = Cfg<T, LOGN, AXIS, V>;
     using C = typename Cx<T>::t;
     using U = typename Unit<T>::U;
     static constexpr int N = Cf::N, E = Cf::E, TF = Cf::TF, NC = Cf::NC, NST = Cf::NST;
@@ -603,17 +574,17 @@ template <typename T, int LOGN, int AXIS, int SHAPE> struct Sweep {
     }
 };
 
-template <typename T, int LOGN, int AXIS, int SHAPE>
-__global__ void __launch_bounds__(Cfg<T, LOGN, AXIS>::THREADS, Cfg<T, LOGN, AXIS>::MINBLK)
+template <typename T, int LOGN, int AXIS, int SHAPE, int V>
+__global__ void __launch_bounds__(Cfg<T, LOGN, AXIS, V>::THREADS, Cfg<T, LOGN, AXIS, V>::MINBLK)
 sweep_kernel(const SweepArgs a) {
-    Sweep<T, LOGN, AXIS, SHAPE>::run(a);
+    Sweep<T, LOGN, AXIS, SHAPE, V>::run(a);
 }
 
-template <typename T, int LOGN, int AXIS, int SHAPE>
+template <typename T, int LOGN, int AXIS, int SHAPE, int V>
 cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
-    using Cf = Cfg<T, LOGN, AXIS>;
+    using Cf = Cfg<T, LOGN, AXIS, V>;
     static bool attr_done = false;
-    auto k = sweep_kernel<T, LOGN, AXIS, SHAPE>;
+    auto k = sweep_kernel<T, LOGN, AXIS, SHAPE, V>;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               Cf::SMEM_BYTES);
@@ -634,11 +605,11 @@ cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, k, a);
 }
 
-// Fills the stage-major twiddle table of an N = 2^LOGN sweep in FP64 (sincospi):
-// FP32 entries are float4 (c_hi, s_hi, c_lo, s_lo), FP64 entries double2 (c, s).
-template <typename T, int LOGN>
+// Fills the stage-major twiddle table of an N = 2^LOGN sweep with 2^LOGE elements per
+// thread in FP64 (sincospi): FP32 entries are float4 (c_hi, s_hi, c_lo, s_lo), FP64
+// entries double2 (c, s).
+template <typename T, int LOGN, int LOGE>
 __global__ void twiddle_kernel(void* out) {
-    constexpr int LOGE = Cfg<T, LOGN, AXIS_X>::LOGE;
     constexpr int NST = plan_nst(LOGN, LOGE);
     const int total = tw_total(LOGN, LOGE);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -670,58 +641,64 @@ __global__ void twiddle_kernel(void* out) {
     }
 }
 
-template <typename T, int LOGN> cudaError_t build_tw(void* out, int* entries, cudaStream_t s) {
-    constexpr int LOGE = Cfg<T, LOGN, AXIS_X>::LOGE;
-    *entries = tw_total(LOGN, LOGE);
-    if (*entries > 0) twiddle_kernel<T, LOGN><<<(*entries + 255) / 256, 256, 0, s>>>(out);
+template <typename T, int LOGN, int LOGE> cudaError_t build_tw(void* out, int* entries, cudaStream_t s) {
+    constexpr int LE = LOGE < LOGN ? LOGE : LOGN;
+    *entries = tw_total(LOGN, LE);
+    if (*entries > 0) twiddle_kernel<T, LOGN, LE><<<(*entries + 255) / 256, 256, 0, s>>>(out);
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t build_twiddles(int logn, void* out, int* entries, cudaStream_t s) {
+template <typename T, int LOGN> cudaError_t build_tw_e(int loge, void* out, int* entries, cudaStream_t s) {
+    if (loge == 2) return build_tw<T, LOGN, 2>(out, entries, s);
+    if (loge == 3) return build_tw<T, LOGN, 3>(out, entries, s);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T> cudaError_t build_twiddles(int logn, int loge, void* out, int* entries, cudaStream_t s) {
     switch (logn) {
-        case 2: return build_tw<T, 2>(out, entries, s);
-        case 3: return build_tw<T, 3>(out, entries, s);
-        case 4: return build_tw<T, 4>(out, entries, s);
-        case 5: return build_tw<T, 5>(out, entries, s);
-        case 6: return build_tw<T, 6>(out, entries, s);
-        case 7: return build_tw<T, 7>(out, entries, s);
-        case 8: return build_tw<T, 8>(out, entries, s);
-        case 9: return build_tw<T, 9>(out, entries, s);
-        case 10: return build_tw<T, 10>(out, entries, s);
-        case 11: return build_tw<T, 11>(out, entries, s);
-        case 12: return build_tw<T, 12>(out, entries, s);
+        case 2: return build_tw_e<T, 2>(loge, out, entries, s);
+        case 3: return build_tw_e<T, 3>(loge, out, entries, s);
+        case 4: return build_tw_e<T, 4>(loge, out, entries, s);
+        case 5: return build_tw_e<T, 5>(loge, out, entries, s);
+        case 6: return build_tw_e<T, 6>(loge, out, entries, s);
+        case 7: return build_tw_e<T, 7>(loge, out, entries, s);
+        case 8: return build_tw_e<T, 8>(loge, out, entries, s);
+        case 9: return build_tw_e<T, 9>(loge, out, entries, s);
+        case 10: return build_tw_e<T, 10>(loge, out, entries, s);
+        case 11: return build_tw_e<T, 11>(loge, out, entries, s);
+        case 12: return build_tw_e<T, 12>(loge, out, entries, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T, int AXIS, int SHAPE>
+template <typename T, int AXIS, int SHAPE, int V>
 cudaError_t launch_logn(int logn, const SweepArgs& a, cudaStream_t s) {
     switch (logn) {
-        case 2: return launch_one<T, 2, AXIS, SHAPE>(a, s);
-        case 3: return launch_one<T, 3, AXIS, SHAPE>(a, s);
-        case 4: return launch_one<T, 4, AXIS, SHAPE>(a, s);
-        case 5: return launch_one<T, 5, AXIS, SHAPE>(a, s);
-        case 6: return launch_one<T, 6, AXIS, SHAPE>(a, s);
-        case 7: return launch_one<T, 7, AXIS, SHAPE>(a, s);
-        case 8: return launch_one<T, 8, AXIS, SHAPE>(a, s);
-        case 9: return launch_one<T, 9, AXIS, SHAPE>(a, s);
-        case 10: return launch_one<T, 10, AXIS, SHAPE>(a, s);
-        case 11: return launch_one<T, 11, AXIS, SHAPE>(a, s);
-        case 12: return launch_one<T, 12, AXIS, SHAPE>(a, s);
+        case 2: return launch_one<T, 2, AXIS, SHAPE, V>(a, s);
+        case 3: return launch_one<T, 3, AXIS, SHAPE, V>(a, s);
+        case 4: return launch_one<T, 4, AXIS, SHAPE, V>(a, s);
+        case 5: return launch_one<T, 5, AXIS, SHAPE, V>(a, s);
+        case 6: return launch_one<T, 6, AXIS, SHAPE, V>(a, s);
+        case 7: return launch_one<T, 7, AXIS, SHAPE, V>(a, s);
+        case 8: return launch_one<T, 8, AXIS, SHAPE, V>(a, s);
+        case 9: return launch_one<T, 9, AXIS, SHAPE, V>(a, s);
+        case 10: return launch_one<T, 10, AXIS, SHAPE, V>(a, s);
+        case 11: return launch_one<T, 11, AXIS, SHAPE, V>(a, s);
+        case 12: return launch_one<T, 12, AXIS, SHAPE, V>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T>
+template <typename T, int V>
 cudaError_t launch_sweep(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s) {
     if (axis == AXIS_X) {
-        if (shape == SHAPE_F1F2) return launch_logn<T, AXIS_X, SHAPE_F1F2>(logn, a, s);
-        if (shape == SHAPE_F1) return launch_logn<T, AXIS_X, SHAPE_F1>(logn, a, s);
-        if (shape == SHAPE_F2) return launch_logn<T, AXIS_X, SHAPE_F2>(logn, a, s);
+        if (shape == SHAPE_F1F2) return launch_logn<T, AXIS_X, SHAPE_F1F2, V>(logn, a, s);
+        if (shape == SHAPE_F1) return launch_logn<T, AXIS_X, SHAPE_F1, V>(logn, a, s);
+        if (shape == SHAPE_F2) return launch_logn<T, AXIS_X, SHAPE_F2, V>(logn, a, s);
     } else {
-        if (shape == SHAPE_F1F2) return launch_logn<T, AXIS_Y, SHAPE_F1F2>(logn, a, s);
-        if (shape == SHAPE_F1) return launch_logn<T, AXIS_Y, SHAPE_F1>(logn, a, s);
-        if (shape == SHAPE_F2) return launch_logn<T, AXIS_Y, SHAPE_F2>(logn, a, s);
+        if (shape == SHAPE_F1F2) return launch_logn<T, AXIS_Y, SHAPE_F1F2, V>(logn, a, s);
+        if (shape == SHAPE_F1) return launch_logn<T, AXIS_Y, SHAPE_F1, V>(logn, a, s);
+        if (shape == SHAPE_F2) return launch_logn<T, AXIS_Y, SHAPE_F2, V>(logn, a, s);
     }
     return cudaErrorInvalidValue;
 }

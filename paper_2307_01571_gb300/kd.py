@@ -24,6 +24,7 @@ KD_ERR_NONFINITE, KD_ERR_NORM_DRIFT, KD_ERR_TIMEOUT = -4, -5, -6
 KD_ERR_STATE_MISMATCH, KD_ERR_NOMEM = -7, -8
 KD_FP64, KD_FP32 = 0, 1
 KD_HOST, KD_DEVICE = 0, 1
+KD_SWEEP_VARIANTS, KD_TUNE_FORCE = 4, 1
 
 
 class KdError(RuntimeError):
@@ -92,6 +93,10 @@ _SIGS = {
     "kd_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "kd_bench_sweep": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "kd_get_launch_count": (C.c_int, [_vp, _P(C.c_int64)]),
+    "kd_autotune": (C.c_int, [_vp, C.c_double, C.c_int32, C.c_int32, _P(C.c_int32), _P(C.c_int32),
+                              _P(C.c_float)]),
+    "kd_set_sweep_variants": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "kd_get_sweep_variants": (C.c_int, [_vp, _P(C.c_int32), _P(C.c_int32)]),
     "kd_density_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                      C.c_double, _vp, _vp, _vp]),
     "kd_batch_create": (C.c_int, [_P(_vp), C.c_int32, _vp, _P(_vp)]),
@@ -241,6 +246,27 @@ class Sim:
 
     def bench_sweep(self, kind: int, reps: int):
         _check(kd_bench_sweep(self._h, kind, reps))
+
+    def autotune(self, dt: float, reps: int = 20, force: bool = False) -> dict:
+        """Times the launch variants of both sweeps (``kd_autotune``) and applies the
+        fastest; returns {"variants": (x, y), "ms": {"x": [...], "y": [...]}} (the recorded
+        times when the choice came from the process-wide record; -1 for FP64)."""
+        vx, vy = C.c_int32(), C.c_int32()
+        ms = (C.c_float * (2 * KD_SWEEP_VARIANTS))()
+        _check(kd_autotune(self._h, dt, reps, KD_TUNE_FORCE if force else 0, C.byref(vx),
+                           C.byref(vy), ms))
+        return {"variants": (vx.value, vy.value),
+                "ms": {"x": list(ms[:KD_SWEEP_VARIANTS]), "y": list(ms[KD_SWEEP_VARIANTS:])}}
+
+    @property
+    def sweep_variants(self) -> tuple:
+        vx, vy = C.c_int32(), C.c_int32()
+        _check(kd_get_sweep_variants(self._h, C.byref(vx), C.byref(vy)))
+        return vx.value, vy.value
+
+    @sweep_variants.setter
+    def sweep_variants(self, v):
+        _check(kd_set_sweep_variants(self._h, int(v[0]), int(v[1])))
 
     def launch_count(self) -> int:
         n = C.c_int64()

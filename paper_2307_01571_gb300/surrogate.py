@@ -75,6 +75,7 @@ def solve(rows, batch: int = 256, stream=None, **wkw):
         sims = [kd.Sim.from_workload(w, stream=stream) for w in wls]
         for s, w in zip(sims, wls):
             s.init_packet(w.packet)
+            s.autotune(w.dt)      # launch variants of this grid (timed once per process)
         with kd.Batch(sims, stream=stream) as b:
             b.step([w.dt for w in wls], wls[0].nsteps)
         for i, (s, r) in enumerate(zip(sims, chunk)):

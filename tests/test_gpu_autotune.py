@@ -1,0 +1,144 @@
+"""The FFT autotuner and the launch variants it chooses among: every variant of both
+sweeps against the oracle (several tiles and a ragged tail, and the 1024x512 benchmark
+grid), bitwise identity of variants that differ only in threads per CTA, and the
+tuner's contract (state untouched, process-wide record, forced re-timing, FP64 single
+variant)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_01571_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2307_01571_gb300 import _build
+    _build.build()
+    from paper_2307_01571_gb300 import kd as mod
+    return mod
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.complex128) - b)) / np.max(np.abs(b)))
+
+
+# variants 0 and 1 differ only in threads per CTA (same per-line arithmetic, bitwise
+# identical); variant 2 runs radix-4 stages and variant 3 changes the components per CTA,
+# where the compiler may fuse the pointwise ops' multiply-adds differently (last-ulp
+# differences, same accuracy)
+SAME_ARITHMETIC = (0, 1)
+
+
+def run(kd, wl, psi, variants, nsteps):
+    with kd.Sim(wl.units, wl.grid, wl.field, 1) as sim:
+        sim.sweep_variants = variants
+        assert sim.sweep_variants == tuple(variants)
+        sim.set_spinor(psi)
+        sim.step(wl.dt, nsteps)
+        return sim.get_spinor()
+
+
+@pytest.mark.parametrize("nx,ny", [(4, 4), (8, 64), (32, 16), (64, 128), (256, 32), (2048, 8), (8, 1024)])
+def test_every_variant_against_oracle(kd, nx, ny):
+    wl = W.small(nx, ny, W.GAUSS, units=W.ATOMIC, a0=0.4, nsteps=5)
+    psi = W.random_spinor(nx, ny, 11 * nx + ny)
+    ref = oracle.step(wl.units, wl.grid, wl.field, psi, 0.0, wl.dt, 5)
+    outs = {}
+    for vx in range(kd.KD_SWEEP_VARIANTS):
+        for vy in range(kd.KD_SWEEP_VARIANTS):
+            got = run(kd, wl, psi, (vx, vy), 5)
+            assert rel(got, ref) <= 1e-4, (vx, vy)
+            outs[(vx, vy)] = got
+    base = outs[(0, 0)]
+    for vx in SAME_ARITHMETIC:
+        for vy in SAME_ARITHMETIC:
+            assert np.array_equal(outs[(vx, vy)], base), (vx, vy)
+
+
+def test_variants_at_1024x512_against_oracle(kd):
+    wl = W.c2(precision=1, nsteps=3)
+    u, g, f, pk = wl.units, wl.grid, wl.field, wl.packet
+    ref = oracle.step(u, g, f, oracle.init_packet(u, g, f, pk), 0.0, wl.dt, 3)
+    outs = []
+    for v in range(kd.KD_SWEEP_VARIANTS):
+        with kd.Sim.from_workload(wl) as sim:
+            sim.sweep_variants = (v, v)
+            sim.init_packet(pk)
+            obs = sim.step(wl.dt, 3)
+            got = sim.get_spinor()
+        assert rel(got, ref) <= 1e-4, v
+        outs.append(got)
+    for v in SAME_ARITHMETIC:
+        assert np.array_equal(outs[v], outs[0]), v
+
+
+def test_autotune_contract(kd):
+    wl = W.small(256, 128, W.GAUSS, units=W.ATOMIC, a0=0.3)
+    with kd.Sim.from_workload(wl.with_(precision=1)) as sim:
+        sim.init_packet(wl.packet)
+        before = sim.get_spinor()
+        r = sim.autotune(wl.dt, reps=8, force=True)
+        vx, vy = r["variants"]
+        assert 0 <= vx < kd.KD_SWEEP_VARIANTS and 0 <= vy < kd.KD_SWEEP_VARIANTS
+        assert sim.sweep_variants == (vx, vy)
+        for ax, v in (("x", vx), ("y", vy)):
+            ms = r["ms"][ax]
+            assert all(m > 0 for m in ms), ms
+            assert v == 0 or ms[v] < 0.98 * ms[0]
+        # the tuner reads the state and writes only scratch
+        assert np.array_equal(sim.get_spinor(), before)
+        # a tuned simulation steps like the oracle
+        sim.step(wl.dt, 6)
+        got = sim.get_spinor()
+    ref = oracle.step(wl.units, wl.grid, wl.field, before, 0.0, wl.dt, 6)
+    assert rel(got, ref) <= 1e-4
+    # a second simulation of the same shape takes the recorded choice without timing
+    with kd.Sim.from_workload(wl.with_(precision=1)) as sim2:
+        r2 = sim2.autotune(wl.dt * 2, reps=8)
+        assert r2["variants"] == (vx, vy)
+        assert r2["ms"] == r["ms"]
+    # FP64 has the one variant
+    with kd.Sim.from_workload(wl.with_(precision=0)) as s64:
+        r3 = s64.autotune(wl.dt, reps=2)
+        assert r3["variants"] == (0, 0)
+        with pytest.raises(kd.KdError):
+            s64.sweep_variants = (1, 0)
+
+
+def test_autotune_rejects_bad_arguments(kd):
+    wl = W.small(16, 16, W.GAUSS)
+    with kd.Sim.from_workload(wl.with_(precision=1)) as sim:
+        for dt, reps, flags in [(0.0, 4, 0), (wl.dt, 0, 0), (wl.dt, 4, 8)]:
+            with pytest.raises(kd.KdError) as e:
+                kd._check(kd.kd_autotune(sim.handle, dt, reps, flags, None, None, None))
+            assert e.value.code == kd.KD_ERR_ARG
+        for v in [(-1, 0), (0, 4)]:
+            with pytest.raises(kd.KdError):
+                sim.sweep_variants = v
+        assert sim.sweep_variants == (0, 0)
+
+
+def test_batch_of_tuned_members_matches_members_alone(kd):
+    wls = [W.small(128, 64, W.GAUSS, units=W.ATOMIC, a0=0.2), W.small(64, 256, W.GAUSS, units=W.ATOMIC)]
+    variants = [(1, 2), (3, 1)]
+    alone = []
+    for wl, v in zip(wls, variants):
+        with kd.Sim.from_workload(wl.with_(precision=1)) as sim:
+            sim.sweep_variants = v
+            sim.init_packet(wl.packet)
+            sim.step(wl.dt, 30)
+            alone.append(sim.get_spinor())
+    sims = [kd.Sim.from_workload(wl.with_(precision=1)) for wl in wls]
+    for s, wl, v in zip(sims, wls, variants):
+        s.sweep_variants = v
+        s.init_packet(wl.packet)
+    with kd.Batch(sims) as b:
+        b.step([wl.dt for wl in wls], 30)
+    for s, a in zip(sims, alone):
+        assert np.array_equal(s.get_spinor(), a)
+        s.close()
