@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-surrogate", action="store_true")
+    p.add_argument("--no-tc", action="store_true", help="skip the tensor-core precision form")
     return p.parse_args()
 
 
@@ -237,6 +238,58 @@ def batched_form(kd, stream, K, barrier, dist):
     return res
 
 
+def precision_form(kd, stream, with_oracle: bool):
+    """Precision form on the 2048x1024 grid: the 1024-point (y) sweeps as tensor-core DFT
+    products (KD_FP32_TC), the 2048-point (x) sweeps on the CUDA cores, against the FP32
+    CUDA-core form on the same run; error of both against the oracle after 2 Strang steps."""
+    import torch
+    wl = W.c3(precision=W.FP32_TC)
+    res = {"workload": wl.name, "grid": [wl.grid.nx, wl.grid.ny]}
+    for prec, name in ((W.FP32_TC, "tc"), (W.FP32, "fp32")):
+        w = wl.with_(precision=prec)
+        sim = kd.Sim.from_workload(w, stream=stream.cuda_stream)
+        sim.init_packet(w.packet)
+        sim.autotune(w.dt)
+        n0 = sim.observe()["norm"]
+        sim.step(w.dt, w.nsteps, obs_every=w.obs_every)      # warm-up (graphs captured)
+        sim.init_packet(w.packet)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        obs = sim.step(w.dt, w.nsteps, obs_every=w.obs_every)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        sweep = {}
+        for kind, nm in ((0, "x_sweep"), (1, "y_sweep")):
+            sim.bench_sweep(kind, 100)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.bench_sweep(kind, 100)
+            b.record(stream)
+            b.synchronize()
+            sweep[nm] = round(a.elapsed_time(b) / 100, 5)
+        sim.close()
+        res[name] = {"value": w.points * w.nsteps / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms,
+                     "norm_drift": max(abs(o["norm"] - n0) for o in obs), "launch_ms": sweep}
+    res["tc_over_fp32"] = res["tc"]["value"] / res["fp32"]["value"]
+    if with_oracle:
+        wlo = wl.with_(precision=W.FP64, nsteps=2)
+        _, _, ref = oracle_rate(wlo, 2)
+        errs = {}
+        for prec, name in ((W.FP32_TC, "tc"), (W.FP32, "fp32")):
+            sim = kd.Sim.from_workload(wlo.with_(precision=prec), stream=stream.cuda_stream)
+            sim.init_packet(wlo.packet)
+            sim.step(wlo.dt, 2)
+            got = sim.get_spinor().astype(np.complex128)
+            sim.close()
+            errs[name] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        errs.update({"strang_steps": 2, "measure": "max|psi-psi_oracle|/max|psi_oracle|"})
+        res["error_vs_oracle"] = errs
+    return res
+
+
 def surrogate_form(n_runs: int = 4096):
     """Config 5: the MLP surrogate (5 -> 3 x 256 GELU -> 4) trained by the library's own
     kernels on n_runs batched-solver runs (seeded uniform draws, 256x128, 2000 steps),
@@ -406,6 +459,11 @@ def main():
                         "norm_drift": drift64, "speedup_fp32_over_fp64": value / v64,
                         "roofline": roofline_alu(wl64, sw64),
                         "roofline_hbm": roofline("fp64", wl64, sw64, hbm), "gpu_launches": l64}
+    if rank == 0 and not args.no_tc:
+        line["precision_form"] = precision_form(kd, stream, not args.no_cpu)
+        if "fp64" in line:
+            line["precision_form"]["speedup_tc_vs_fp64_single"] = (
+                line["precision_form"]["tc"]["value"] / line["fp64"]["value"])
     if not args.no_batch:
         line["batched"] = batched_form(kd, stream, max(1, min(K, 3)), barrier, dist)
         if "fp64" in line:

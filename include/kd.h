@@ -45,6 +45,13 @@ extern "C" {
 
 #define KD_FP64 0 /* complex128 spinor, FP64 arithmetic throughout */
 #define KD_FP32 1 /* complex64 spinor, FP32 arithmetic; FP64-built phase tables */
+/* Precision form: complex64 spinor and tables as KD_FP32, but the full sweeps of axes of
+ * 1024 points evaluate their FFTs as 32-point DFT matrix products on the tensor cores
+ * (four-step 1024 = 32 x 32 FFT of Sec. II.D's transforms; FP16 operands split hi + lo,
+ * three products per term, FP32 accumulation): ~1e-7 relative per stage.  The half sweeps
+ * at run ends and axes of other lengths run the KD_FP32 kernels.  State and checkpoints
+ * are those of KD_FP32 (interchangeable). */
+#define KD_FP32_TC 2
 
 #define KD_HOST 0
 #define KD_DEVICE 1
@@ -112,7 +119,8 @@ typedef struct {
 
 typedef struct kd_sim kd_sim;
 
-/* Creates a simulation on the current CUDA device.  precision is KD_FP64 or KD_FP32.
+/* Creates a simulation on the current CUDA device.  precision is KD_FP64, KD_FP32 or
+ * KD_FP32_TC.
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream) on which every
  * device operation of this simulation is ordered.  The spinor starts at zero, t = 0.
  * Errors: KD_ERR_ARG, KD_ERR_UNSUPPORTED_SIZE, KD_ERR_CUDA, KD_ERR_NOMEM. */
@@ -247,6 +255,16 @@ int kd_autotune(kd_sim* sim, double dt, int32_t reps, int32_t flags, int32_t* va
                 int32_t* variant_y, float* times_ms);
 int kd_set_sweep_variants(kd_sim* sim, int32_t variant_x, int32_t variant_y);
 int kd_get_sweep_variants(kd_sim* sim, int32_t* variant_x, int32_t* variant_y);
+
+/* Test hook for the tensor-core sweeps' bounded waits.  kind KD_FAULT_TC_WAIT: during
+ * the next kd_step call the tensor-core sweeps issue no matrix products, so every wait
+ * for them gives up after its iteration limit (about a second); the kernels then skip
+ * their remaining work, free their tensor memory and set the simulation's status, and
+ * kd_step returns KD_ERR_TIMEOUT with the context intact; the state is then not a valid
+ * evolution (restore a checkpoint or set a new spinor).  kind 0 cancels.  KD_ERR_ARG for other kinds or when the
+ * simulation is not KD_FP32_TC. */
+#define KD_FAULT_TC_WAIT 1
+int kd_inject_fault(kd_sim* sim, int32_t kind);
 
 /* Number of kernel launches this simulation has enqueued so far (graph replays counted
  * node by node). */

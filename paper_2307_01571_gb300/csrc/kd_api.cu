@@ -7,6 +7,7 @@
 // Paper: Ge, Ahrens & Shen, arXiv 2307.01571.  Sec. II.A (field), II.B (Hamiltonian,
 // bispinors, energy), II.C (packet, Fourier convention), II.D (split-operator step),
 // III (observables).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -102,6 +103,12 @@ struct kd_sim {
     kd_obs* obs_dev = nullptr;
     int64_t obs_dev_cap = 0;
     int* status = nullptr;
+    // precision form: tensor-core sweeps of 1024-point axes (KD_FP32_TC)
+    bool tc = false;
+    void* tc_b = nullptr;
+    void* tc_tw = nullptr;
+    float* tc_scale = nullptr;
+    int tc_fault = 0;          // kd_inject_fault: applies to the next kd_step call only
     // host clock: t = t0 + step * dt_clock
     double t0 = 0.0, dt_clock = 0.0;
     int64_t step = 0;
@@ -271,6 +278,37 @@ __global__ void k_norm(const double* rowsum, int ny, double cell, double* scalar
         __syncthreads();
     }
     if (threadIdx.x == 0) scalar[slot] = red[0] * cell;
+}
+
+// Power-of-two operand scales of the tensor-core sweeps from the state's 2-norm
+// S = sqrt(sum |psi|^2) (position space, all components): every FP16 operand stays below
+// 2^14 by the growth bounds of the unnormalised DFTs (an element of a 32-point partial DFT
+// of a vector is at most sqrt(32) times the vector's 2-norm).  out = (x: s_a, s_b,
+// y: s_a, s_b); operands before the pointwise factor carry s_a, after it s_a s_b.
+__global__ void k_tc_scales(const double* rowsum, int nx, int ny, float* out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) acc += rowsum[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double S = sqrt(red[0]);
+    if (!(S > 0.0) || !isfinite(S)) S = 1.0;
+    auto p2 = [](double v) {   // largest power of two <= v, as a float
+        int e = (int)floor(log2(v));
+        e = e < -120 ? -120 : (e > 120 ? 120 : e);
+        return ldexpf(1.0f, e);
+    };
+    const double P = (double)nx * ny;
+    const double sa = 16384.0 / (sqrt(32.0 * nx) * S);
+    out[0] = p2(sa);
+    out[1] = p2(1.0 / sqrt((double)nx));
+    out[2] = p2(sa);
+    out[3] = p2(sqrt(P * nx));
 }
 
 template <typename T>
@@ -552,6 +590,96 @@ template <typename T> int upload_tables_t(kd_sim* s) {
     return KD_OK;
 }
 
+// ------------------------------------------------- precision form tables ---------
+// 32-point DFT matrices for the tensor-core sweeps, in the kernels' shared-memory image:
+// four 64 x 64 FP16 matrices (inverse hi, inverse lo, forward hi, forward lo), each in the
+// dense no-swizzle K-major canonical layout (element (n, k) at byte
+// (n / 8) 1024 + (k / 8) 128 + (n % 8) 16 + (k % 8) 2).  B[2k][2j] = c, B[2k][2j+1] = -s,
+// B[2k+1][2j] = s, B[2k+1][2j+1] = c with c + i s = w_32^(jk) = exp(+-2 pi i jk / 32), all
+// times 2^10 so that the lo parts are normal FP16 numbers.  For each of the 32 angles the
+// lo parts of (c, s) are chosen among +-3 FP16 steps so that (c_hi + c_lo)^2 + (s_hi + s_lo)^2
+// is closest to 2^20: the represented matrix is then unitary far below its rounding
+// (an FP16 hi/lo matrix rounded to nearest loses ~1e-8 of the norm per product).
+constexpr size_t kTcBImageBytes = 4 * 8192;
+
+double h2d(__half h) { return (double)__half2float(h); }
+__half step_half(__half h, int d) {
+    __half_raw r = h;
+    r.x = (unsigned short)(r.x + d);
+    return __half(r);
+}
+
+void unit_pair_half(double c, double s, __half* ch, __half* cl, __half* sh, __half* sl) {
+    *ch = __double2half(c);
+    *sh = __double2half(s);
+    const __half c0 = __double2half(c - h2d(*ch)), s0 = __double2half(s - h2d(*sh));
+    *cl = c0;
+    *sl = s0;
+    const double target = 1024.0 * 1024.0;
+    double best = 1e300;
+    for (int dc = -3; dc <= 3; ++dc)
+        for (int ds = -3; ds <= 3; ++ds) {
+            // stepping the bits of a zero lo part would leave the finite numbers: keep it
+            if ((h2d(c0) == 0.0 && dc) || (h2d(s0) == 0.0 && ds)) continue;
+            const __half cc = step_half(c0, dc), ss = step_half(s0, ds);
+            const double vc = h2d(*ch) + h2d(cc), vs = h2d(*sh) + h2d(ss);
+            const double g = fabs(vc * vc + vs * vs - target) + 1e-6 * (fabs(vc - c) + fabs(vs - s));
+            if (!isfinite(vc) || !isfinite(vs)) continue;
+            if (g < best) { best = g; *cl = cc; *sl = ss; }
+        }
+}
+
+int upload_tc_tables(kd_sim* s) {
+    std::vector<__half> img(kTcBImageBytes / 2);
+    for (int dir = 0; dir < 2; ++dir) {            // 0: inverse (+), 1: forward (-)
+        const double sg = dir == 0 ? 1.0 : -1.0;
+        __half ch[32], cl[32], sh[32], sl[32];
+        for (int m = 0; m < 32; ++m) {
+            const double th = 2.0 * kPi * m / 32.0;
+            unit_pair_half(1024.0 * cos(th), sg * 1024.0 * sin(th), &ch[m], &cl[m], &sh[m], &sl[m]);
+        }
+        for (int part = 0; part < 2; ++part) {     // hi, lo
+            __half* mat = img.data() + (size_t)(2 * dir + part) * 4096;
+            for (int k = 0; k < 32; ++k)
+                for (int j = 0; j < 32; ++j) {
+                    const int m = (j * k) & 31;
+                    const __half c = part ? cl[m] : ch[m], sn = part ? sl[m] : sh[m];
+                    const __half msn = __hneg(sn);
+                    const __half v[4] = {c, msn, sn, c};   // (2k, 2j), (2k, 2j+1), (2k+1, 2j), (2k+1, 2j+1)
+                    for (int q = 0; q < 4; ++q) {
+                        const int n = 2 * k + (q >> 1), kk = 2 * j + (q & 1);
+                        mat[((n >> 3) * 1024 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) / 2] = v[q];
+                    }
+                }
+        }
+    }
+    KD_CUDA(cudaMemcpy(s->tc_b, img.data(), kTcBImageBytes, cudaMemcpyHostToDevice));
+    // twiddles w_1024^m in FP32, the pair within +-3 ulps with |w| closest to 1
+    std::vector<float2> tw(1024);
+    for (int m = 0; m < 1024; ++m) {
+        const double th = 2.0 * kPi * m / 1024.0;
+        const double c = cos(th), sn = sin(th);
+        float bc = (float)c, bs = (float)sn;
+        double best = 1e300;
+        float ci = (float)c;
+        for (int k = 0; k < 3; ++k) ci = nextafterf(ci, -INFINITY);
+        for (int dc = -3; dc <= 3; ++dc, ci = nextafterf(ci, INFINITY)) {
+            float si = (float)sn;
+            for (int k = 0; k < 3; ++k) si = nextafterf(si, -INFINITY);
+            for (int ds = -3; ds <= 3; ++ds, si = nextafterf(si, INFINITY)) {
+                const double g = fabs((double)ci * ci + (double)si * si - 1.0) +
+                                 1e-3 * (fabs(ci - c) + fabs(si - sn));
+                if (g < best) { best = g; bc = ci; bs = si; }
+            }
+        }
+        tw[m] = make_float2(bc, bs);
+    }
+    KD_CUDA(cudaMemcpy(s->tc_tw, tw.data(), 1024 * sizeof(float2), cudaMemcpyHostToDevice));
+    const float one[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+    KD_CUDA(cudaMemcpy(s->tc_scale, one, sizeof one, cudaMemcpyHostToDevice));
+    return KD_OK;
+}
+
 // Tables that depend on dt: the kinetic table (device, FP64) and the per-row
 // (pi_y, cos, sin of the frame phase box_vy p_y dt / hbar).
 // Rounded (cos(ph) - 1, sin(ph)) with |1 + f| = 1 as closely as the precision allows:
@@ -637,7 +765,13 @@ cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* 
     a.mc_f = (float)a.mc;
     a.invP = 1.0 / ((double)s->g.nx * (double)s->g.ny);
     a.invP_f = (float)a.invP;
+    a.tc_b = s->tc_b;
+    a.tc_tw = s->tc_tw;
+    a.tc_scale = s->tc_scale;
+    a.status = s->status;
+    a.tc_fault = s->tc_fault;
     ++s->launches;
+    if (s->tc && shape == SHAPE_F1F2 && tc_supported(logn)) return launch_tc_sweep(axis, a, s->stream);
     return s->prec == KD_FP64 ? launch_sweep_f64(axis, shape, logn, a, s->stream)
                               : launch_sweep_f32(var, axis, shape, logn, a, s->stream);
 }
@@ -646,10 +780,10 @@ cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* 
 // Process-wide record of tuned launch variants per device, grid and field kind, so that
 // simulations of the same shape (the members of a batch, repeated runs) are timed once.
 struct TuneKey {
-    int device, nx, ny, kind, longitudinal;
+    int device, nx, ny, kind, longitudinal, tc;
     bool operator<(const TuneKey& o) const {
-        return std::tie(device, nx, ny, kind, longitudinal) <
-               std::tie(o.device, o.nx, o.ny, o.kind, o.longitudinal);
+        return std::tie(device, nx, ny, kind, longitudinal, tc) <
+               std::tie(o.device, o.nx, o.ny, o.kind, o.longitudinal, o.tc);
     }
 };
 struct TuneResult {
@@ -989,7 +1123,8 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
     g_err.clear();
     if (!units || !grid || !field || !out) return fail(KD_ERR_ARG, "null argument");
     *out = nullptr;
-    if (precision != KD_FP64 && precision != KD_FP32) return fail(KD_ERR_ARG, "precision must be KD_FP64 or KD_FP32");
+    if (precision != KD_FP64 && precision != KD_FP32 && precision != KD_FP32_TC)
+        return fail(KD_ERR_ARG, "precision must be KD_FP64, KD_FP32 or KD_FP32_TC");
     if (!pow2_in_range(grid->nx) || !pow2_in_range(grid->ny))
         return fail(KD_ERR_UNSUPPORTED_SIZE, "nx=%d ny=%d: need powers of two in [4, 4096]", grid->nx, grid->ny);
     if (!(grid->x_max > grid->x_min) || !(grid->y_max > grid->y_min) || !isfinite(grid->x_min) ||
@@ -1017,7 +1152,8 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
     s->u = *units;
     s->g = *grid;
     s->f = *field;
-    s->prec = precision;
+    s->tc = precision == KD_FP32_TC;       // FP32 storage and tables, tensor-core sweeps
+    s->prec = s->tc ? KD_FP32 : precision;
     s->tsize = precision == KD_FP64 ? 8 : 4;
     s->stream = (cudaStream_t)cuda_stream;
     s->device = dev;
@@ -1047,6 +1183,11 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
     KD_ALLOC(s->rowsum, (size_t)grid->ny * sizeof(double));
     KD_ALLOC(s->scalar, 4 * sizeof(double));
     KD_ALLOC(s->status, sizeof(int));
+    if (s->tc) {
+        KD_ALLOC(s->tc_b, kTcBImageBytes);
+        KD_ALLOC(s->tc_tw, 1024 * sizeof(float2));
+        KD_ALLOC(s->tc_scale, 4 * sizeof(float));
+    }
 #undef KD_ALLOC
     if (cudaMemset(s->psi, 0, spinor_bytes(s)) != cudaSuccess ||
         cudaMemset(s->clock, 0, sizeof(Clock)) != cudaSuccess ||
@@ -1055,6 +1196,10 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
         return bail(fail(KD_ERR_CUDA, "memset failed"));
     int rc = precision == KD_FP64 ? upload_tables_t<double>(s) : upload_tables_t<float>(s);
     if (rc) return bail(rc);
+    if (s->tc) {
+        rc = upload_tc_tables(s);
+        if (rc) return bail(rc);
+    }
     rc = warm_variants(s);
     if (rc) return bail(rc);
     *out = s;
@@ -1068,7 +1213,7 @@ void kd_destroy(kd_sim* s) {
     clear_graphs(s);
     void* bufs[] = {s->psi, s->work, s->tw[0][0], s->tw[0][1], s->tw[1][0], s->tw[1][1], s->xtab,
                     s->kxtab, s->kytab, s->ktab, s->clock, s->steps, s->rowsum, s->md, s->scalar,
-                    s->obs_dev, s->status};
+                    s->obs_dev, s->status, s->tc_b, s->tc_tw, s->tc_scale};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -1256,9 +1401,16 @@ int enqueue_prologue(kd_sim* s, const StepPlan& p) {
     k_set_clock<<<1, 1, 0, s->stream>>>(s->clock, 0);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
-    if (p.nobs > 0) {
+    if (s->tc) {
+        int rc = rowsum_launch(s, s->psi);
+        if (rc) return rc;
+        k_tc_scales<<<1, 256, 0, s->stream>>>(s->rowsum, s->g.nx, s->g.ny, s->tc_scale);
+        KD_CUDA(cudaGetLastError());
+        ++s->launches;
+    }
+    if (p.nobs > 0 || s->tc) {
         KD_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), s->stream));
-        if (s->watch_tol > 0) {
+        if (p.nobs > 0 && s->watch_tol > 0) {
             int rc = rowsum_launch(s, s->psi);
             if (rc) return rc;
             k_norm<<<1, 256, 0, s->stream>>>(s->rowsum, s->g.ny, dxdy(s), s->scalar, 1);
@@ -1301,15 +1453,17 @@ template <typename F> int for_each_chunk(const StepPlan& p, F fn) {
 // watchdog status into a return code.
 int finish_step(kd_sim* s, const StepPlan& p, kd_obs* obs_out, int64_t* n_obs) {
     s->step += p.nsteps;
-    if (p.nobs > 0) {
-        if (p.cap > 0)
+    if (p.nobs > 0 || s->tc) {
+        if (p.nobs > 0 && p.cap > 0)
             KD_CUDA(cudaMemcpyAsync(obs_out, s->obs_dev, p.cap * sizeof(kd_obs), cudaMemcpyDeviceToHost, s->stream));
         int st = 0;
         KD_CUDA(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
         KD_CUDA(cudaStreamSynchronize(s->stream));
         if (n_obs) *n_obs = p.nobs;
-        if (st & 1) return fail(KD_ERR_NONFINITE, "non-finite norm observed");
-        if (st & 2) return fail(KD_ERR_NORM_DRIFT, "norm drift beyond %g", s->watch_tol);
+        if (st & KD_STATUS_TC_TIMEOUT)
+            return fail(KD_ERR_TIMEOUT, "tensor-core sweep: a wait for the matrix products gave up");
+        if (st & KD_STATUS_NONFINITE) return fail(KD_ERR_NONFINITE, "non-finite norm observed");
+        if (st & KD_STATUS_DRIFT) return fail(KD_ERR_NORM_DRIFT, "norm drift beyond %g", s->watch_tol);
     }
     return KD_OK;
 }
@@ -1332,7 +1486,22 @@ int kd_step(kd_sim* s, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs
         return run_chunk(s, p.dt, chunk, last, obs, p.w, p.obs_every, p.cap);
     });
     if (rc) return rc;
-    return finish_step(s, p, obs_out, n_obs);
+    rc = finish_step(s, p, obs_out, n_obs);
+    if (s->tc_fault) {   // an injected fault lasts one call (finish_step has synchronised)
+        s->tc_fault = 0;
+        clear_graphs(s);
+    }
+    return rc;
+}
+
+int kd_inject_fault(kd_sim* s, int32_t kind) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (kind != 0 && kind != KD_FAULT_TC_WAIT) return fail(KD_ERR_ARG, "unknown fault kind %d", kind);
+    if (kind == KD_FAULT_TC_WAIT && !s->tc) return fail(KD_ERR_ARG, "not a KD_FP32_TC simulation");
+    s->tc_fault = kind == KD_FAULT_TC_WAIT;
+    clear_graphs(s);
+    return KD_OK;
 }
 
 }  // extern "C"
@@ -1624,7 +1793,7 @@ int kd_autotune(kd_sim* s, double dt, int32_t reps, int32_t flags, int32_t* vari
         rc = kd_set_sweep_variants(s, 0, 0);
         if (rc) return rc;
     } else {
-        const TuneKey key{s->device, s->g.nx, s->g.ny, s->f.kind, s->f.longitudinal};
+        const TuneKey key{s->device, s->g.nx, s->g.ny, s->f.kind, s->f.longitudinal, (int)s->tc};
         bool cached = false;
         if (!(flags & KD_TUNE_FORCE)) {
             std::lock_guard<std::mutex> lk(g_tune_mu);

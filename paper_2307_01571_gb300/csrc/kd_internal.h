@@ -63,7 +63,18 @@ struct SweepArgs {
     const void* kxtab;    // [nx] pi_x
     const void* kytab;    // [ny] (pi_y, cos, sin of the frame phase, pad)
     double mc;            // m c
+    // precision form (tensor-core sweeps of 1024-point axes, kd_tc.cu)
+    const void* tc_b;     // 32-point DFT matrices (inverse hi, lo, forward hi, lo), FP16,
+                          // times 2^10, in the kernel's shared-memory image (32 KiB)
+    const void* tc_tw;    // [1024] float2 (cos, sin) of 2 pi m / 1024
+    const float* tc_scale;  // [axis][2] power-of-two operand scales, set per kd_step
+    int* status;          // error word of the simulation (KD_STATUS_* bits)
+    int tc_fault;         // test hook (kd_inject_fault): the tensor-core sweep issues no
+                          // matrix products, so that its bounded waits run out
 };
+
+// bits of the device status word
+constexpr int KD_STATUS_NONFINITE = 1, KD_STATUS_DRIFT = 2, KD_STATUS_TC_TIMEOUT = 16;
 
 // Launch variants of the FP32 sweeps, timed per grid by the autotuner (kd_autotune);
 // variant 0 is the default.  A variant fixes the radix schedule (loge = log2 of the
@@ -108,6 +119,10 @@ cudaError_t launch_sweep_f32_v(int axis, int shape, int logn, const SweepArgs& a
 cudaError_t launch_sweep_f32(int variant, int axis, int shape, int logn, const SweepArgs& a,
                              cudaStream_t s);
 cudaError_t launch_sweep_f64(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
+// Precision form: whether an axis of 2^logn points has the tensor-core sweep, and its
+// launch (full sweeps only; persistent, at most two CTAs per SM).
+bool tc_supported(int logn);
+cudaError_t launch_tc_sweep(int axis, const SweepArgs& a, cudaStream_t s);
 // Fills the stage-major twiddle table of an N = 2^logn sweep whose threads own 2^loge
 // elements (at most 2N entries of 16 B) and returns the number of entries.
 cudaError_t build_twiddles_f32(int logn, int loge, void* out, int* entries, cudaStream_t s);

@@ -22,9 +22,10 @@ KD_OK = 0
 KD_ERR_ARG, KD_ERR_UNSUPPORTED_SIZE, KD_ERR_CUDA = -1, -2, -3
 KD_ERR_NONFINITE, KD_ERR_NORM_DRIFT, KD_ERR_TIMEOUT = -4, -5, -6
 KD_ERR_STATE_MISMATCH, KD_ERR_NOMEM = -7, -8
-KD_FP64, KD_FP32 = 0, 1
+KD_FP64, KD_FP32, KD_FP32_TC = 0, 1, 2
 KD_HOST, KD_DEVICE = 0, 1
 KD_SWEEP_VARIANTS, KD_TUNE_FORCE = 4, 1
+KD_FAULT_TC_WAIT = 1
 
 
 class KdError(RuntimeError):
@@ -96,6 +97,7 @@ _SIGS = {
     "kd_autotune": (C.c_int, [_vp, C.c_double, C.c_int32, C.c_int32, _P(C.c_int32), _P(C.c_int32),
                               _P(C.c_float)]),
     "kd_set_sweep_variants": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "kd_inject_fault": (C.c_int, [_vp, C.c_int32]),
     "kd_get_sweep_variants": (C.c_int, [_vp, _P(C.c_int32), _P(C.c_int32)]),
     "kd_density_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                      C.c_double, _vp, _vp, _vp]),
@@ -267,6 +269,11 @@ class Sim:
     @sweep_variants.setter
     def sweep_variants(self, v):
         _check(kd_set_sweep_variants(self._h, int(v[0]), int(v[1])))
+
+    def inject_fault(self, kind: int = KD_FAULT_TC_WAIT):
+        """Test hook (``kd_inject_fault``): the next ``step`` call's tensor-core sweeps issue
+        no matrix products, so their bounded waits run out and ``step`` raises KD_ERR_TIMEOUT."""
+        _check(kd_inject_fault(self._h, kind))
 
     def launch_count(self) -> int:
         n = C.c_int64()

@@ -18,7 +18,7 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 NONE, PLANE, GAUSS = 0, 1, 2
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_TC = 0, 1, 2
 
 
 @dataclass(frozen=True)
