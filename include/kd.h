@@ -242,8 +242,9 @@ int kd_bench_sweep(kd_sim* sim, int32_t kind, int32_t reps);
  * KD_TUNE_FORCE times again).  variant_x / variant_y (may be NULL) receive the choice,
  * times_ms (may be NULL, 2 * KD_SWEEP_VARIANTS floats: x then y) the measured ms per
  * launch (the recorded ones when the choice was looked up; -1 for FP64).  FP64
- * simulations have one variant (0).  Synchronises the simulation's stream; must not be called while the
- * stream is being captured.  Variants 0 and 1 differ only in threads per CTA and give
+ * simulations have one variant (0).  Synchronises the simulation's stream: KD_ERR_ARG
+ * while that stream is being captured (kd_set_sweep_variants likewise, when it changes the
+ * variants).  Variants 0 and 1 differ only in threads per CTA and give
  * bitwise identical results; the radix-4 schedule (2) and the components-per-CTA change
  * (3) round differently in the last bits (every variant meets the same accuracy).  A
  * simulation's results are reproducible for fixed variants.  kd_set_sweep_variants selects variants directly

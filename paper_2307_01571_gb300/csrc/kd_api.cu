@@ -793,6 +793,19 @@ struct TuneResult {
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneResult> g_tune;
 
+// KD_ERR_ARG when the simulation's stream is being captured (for calls that launch and
+// synchronise outside the step loop)
+int reject_capture(kd_sim* s, const char* what) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return KD_OK;
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(KD_ERR_ARG, "%s: the simulation's stream is being captured", what);
+    return KD_OK;
+}
+
 // First launch of every sweep shape of the current variants outside any stream capture
 // (sets the kernels' shared-memory attributes); reads psi, writes only the work buffer.
 int warm_variants(kd_sim* s) {
@@ -1766,6 +1779,8 @@ int kd_set_sweep_variants(kd_sim* s, int32_t variant_x, int32_t variant_y) {
     if (variant_x < 0 || variant_x >= nv || variant_y < 0 || variant_y >= nv)
         return fail(KD_ERR_ARG, "sweep variant out of range [0, %d)", nv);
     if (s->var[0] == variant_x && s->var[1] == variant_y) return KD_OK;
+    rc = reject_capture(s, "kd_set_sweep_variants");
+    if (rc) return rc;
     s->var[0] = variant_x;
     s->var[1] = variant_y;
     clear_graphs(s);
@@ -1786,6 +1801,8 @@ int kd_autotune(kd_sim* s, double dt, int32_t reps, int32_t flags, int32_t* vari
     if (!(dt > 0) || !isfinite(dt)) return fail(KD_ERR_ARG, "dt must be positive and finite");
     if (reps < 1 || reps > 4096) return fail(KD_ERR_ARG, "reps must be in [1, 4096]");
     if (flags & ~KD_TUNE_FORCE) return fail(KD_ERR_ARG, "unknown flags");
+    rc = reject_capture(s, "kd_autotune");
+    if (rc) return rc;
     TuneResult res{};
     for (auto& a : res.ms)
         for (float& m : a) m = -1.0f;

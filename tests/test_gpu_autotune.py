@@ -142,3 +142,25 @@ def test_batch_of_tuned_members_matches_members_alone(kd):
     for s, a in zip(sims, alone):
         assert np.array_equal(s.get_spinor(), a)
         s.close()
+
+
+def test_tuning_is_rejected_during_stream_capture(kd):
+    """The tuner times launches and synchronises the simulation's stream, which a stream
+    capture does not allow: it returns KD_ERR_ARG and leaves the capture intact."""
+    import torch
+    wl = W.small(64, 64, W.GAUSS)
+    s = torch.cuda.Stream()
+    with kd.Sim.from_workload(wl.with_(precision=1), stream=s.cuda_stream) as sim:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            g.capture_begin()
+            try:
+                with pytest.raises(kd.KdError) as e1:
+                    sim.autotune(wl.dt, reps=2, force=True)
+                with pytest.raises(kd.KdError) as e2:
+                    sim.sweep_variants = (1, 1)
+            finally:
+                g.capture_end()
+        assert e1.value.code == kd.KD_ERR_ARG and e2.value.code == kd.KD_ERR_ARG
+        assert sim.sweep_variants == (0, 0)
+        assert sim.autotune(wl.dt, reps=2, force=True)["variants"] is not None
