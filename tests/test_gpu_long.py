@@ -16,8 +16,11 @@ from paper_2307_01571_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-# relative error bound after n steps per precision
-TOL = {0: 1e-10, 1: 1e-4, 2: 1e-2}
+# relative error bound over the runs per precision: the FP64 and FP32 bars of the short
+# tests (measured at 2000 steps: 6e-13 and 3.3e-6); the precision form's tensor cores
+# truncate in their FP32 accumulation, so its norm decays by ~7e-7 per step and its error
+# grows with it (measured 1.3e-4 after 200 steps, 1.4e-3 after 2000): stated bound 3e-3
+TOL = {0: 1e-10, 1: 1e-4, 2: 3e-3}
 
 
 def records(name):
