@@ -293,6 +293,36 @@ def precision_form(kd, stream, with_oracle: bool):
     return res
 
 
+def full_run_errors(kd, stream, precisions):
+    """Error of the benchmark run itself (1024x512, 2000 Strang steps, observations every
+    100) against the oracle's stored record of the same run (tests/golden/c2_long_oracle.json,
+    written by tests/golden/make_long_runs.py from the oracle alone), at its 256 sampled
+    points, relative to the oracle's max |psi|."""
+    path = os.path.join(ROOT, "tests", "golden", "c2_long_oracle.json")
+    try:
+        with open(path) as fh:
+            rec = [r for r in json.load(fh)["records"] if r["steps"] == 2000][0]
+    except Exception:
+        return None
+    pts = np.array(rec["points_yx"])
+    ref = np.array(rec["psi"])
+    ref = ref[..., 0] + 1j * ref[..., 1]
+    out = {}
+    for prec, name in precisions:
+        wl = W.c2(precision=prec)
+        sim = kd.Sim.from_workload(wl, stream=stream.cuda_stream)
+        sim.init_packet(wl.packet)
+        obs = sim.step(wl.dt, wl.nsteps, obs_every=wl.obs_every)
+        got = sim.get_spinor()[pts[:, 0], pts[:, 1], :].astype(np.complex128)
+        sim.close()
+        out[name] = {"psi": float(np.max(np.abs(got - ref)) / rec["max_abs_psi"]),
+                     "pop_diff": abs(obs[-1]["pop_diff"] - rec["obs"]["pop_diff"]) / rec["obs"]["pop_diff"],
+                     "cm_target": abs(obs[-1]["cm_target"] - rec["obs"]["cm_target"]) / max(rec["obs"]["cm_target"], 1e-300)}
+    out.update({"strang_steps": 2000, "points": len(pts),
+                "measure": "max|psi-psi_oracle|/max|psi_oracle| at the record's points; relative read-out errors"})
+    return out
+
+
 def surrogate_form(n_runs: int = 4096):
     """Config 5: the MLP surrogate (5 -> 3 x 256 GELU -> 4) trained by the library's own
     kernels on n_runs batched-solver runs (seeded uniform draws, 256x128, 2000 steps),
@@ -496,6 +526,11 @@ def main():
             s.close()
             errs[name] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
         line["error_vs_oracle"] = {**errs, "strang_steps": 4, "measure": "max|psi-psi_oracle|/max|psi_oracle|"}
+        forms = [(W.FP32, "fp32")] + ([] if args.no_fp64 else [(W.FP64, "fp64")]) + \
+                ([] if args.no_tc else [(W.FP32_TC, "fp32_tc")])
+        fr = full_run_errors(kd, stream, forms)
+        if fr:
+            line["error_vs_oracle"]["full_run"] = fr
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"4 Strang steps of the 1024x512 FP64 run ({dt:.1f} s)"}
     if dist:
