@@ -211,6 +211,9 @@ def batched_form(kd, stream, K, barrier, dist):
     dts = [w.dt for w in members]
     res = {"sweep_variants": chosen}
     with kd.Batch(sims, stream=stream.cuda_stream) as b:
+        # launch variants timed on the batch as a whole (members' states are kept)
+        bv = b.autotune(dts, steps=20)
+        res["sweep_variants_batch"] = {f"{w.grid.nx}x{w.grid.ny}": v for w, v in zip(members, bv)}
         b.step(dts, members[0].nsteps, obs_every=100)           # warm-up: graphs captured
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -220,7 +223,8 @@ def batched_form(kd, stream, K, barrier, dist):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / K
-    for s_, w in zip(sims, members):                           # the same runs one by one
+    for s_, w in zip(sims, members):                           # the same runs one by one,
+        s_.autotune(w.dt)                                      # on the variants tuned alone
         s_.step(w.dt, w.nsteps, obs_every=100)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

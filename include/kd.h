@@ -197,6 +197,16 @@ int kd_batch_create(kd_sim* const* sims, int32_t n, void* cuda_stream, kd_batch*
 int kd_batch_step(kd_batch* batch, const double* dt, int64_t nsteps, int64_t obs_every,
                   kd_obs* obs_out, int64_t obs_cap, int64_t* n_obs);
 void kd_batch_destroy(kd_batch* batch);
+/* Batch-aware FFT autotuner: members advanced together compete for the GPU, so the launch
+ * variants that are fastest for a grid alone (kd_autotune) need not be fastest in the
+ * batch.  For each axis and each group of members with the same grid and form (FP64
+ * members excepted), every variant is timed over `steps` steps of the whole batch (after
+ * one untimed run that captures the graphs), and kept when the batch is more than 2 %
+ * faster.  The members' states, times and step counts are restored afterwards (each
+ * member's work buffer holds its state meanwhile); only the variants change.  variants
+ * (may be NULL) receives 2 ints per member (x, y).  steps in [1, 4096]; synchronises;
+ * KD_ERR_ARG while the batch's or a member's stream is being captured. */
+int kd_batch_autotune(kd_batch* batch, const double* dt, int32_t steps, int32_t* variants);
 
 /* Surrogate network (a learned stand-in for the solver's read-outs; the paper has no network): a fully
  * connected MLP, widths[0] inputs -> ... -> widths[nlayers] outputs, exact-erf GELU on the

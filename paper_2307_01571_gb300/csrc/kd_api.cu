@@ -1667,6 +1667,120 @@ int kd_batch_step(kd_batch* b, const double* dt, int64_t nsteps, int64_t obs_eve
     return first_err;
 }
 
+int kd_batch_autotune(kd_batch* b, const double* dt, int32_t steps, int32_t* variants) {
+    if (!b || !dt) return fail(KD_ERR_ARG, "null batch or dt");
+    if (steps < 1 || steps > 4096) return fail(KD_ERR_ARG, "steps must be in [1, 4096]");
+    KD_CUDA(cudaSetDevice(b->device));
+    const size_t n = b->sims.size();
+    for (size_t i = 0; i < n; ++i) {
+        if (!(dt[i] > 0) || !isfinite(dt[i])) return fail(KD_ERR_ARG, "dt[%zu] must be positive and finite", i);
+        int rc = reject_capture(b->sims[i], "kd_batch_autotune");
+        if (rc) return rc;
+    }
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(b->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            return fail(KD_ERR_ARG, "kd_batch_autotune: the batch stream is being captured");
+        cudaGetLastError();
+    }
+    // every compiled variant launched once outside any capture (kernel attributes), then
+    // the current variants back; warm_variants writes only the work buffers
+    std::vector<std::pair<int, int>> keep(n);
+    for (size_t i = 0; i < n; ++i) {
+        kd_sim* s = b->sims[i];
+        keep[i] = {s->var[0], s->var[1]};
+        if (s->prec == KD_FP64) continue;
+        for (int v = 0; v < KD_SWEEP_VARIANTS; ++v) {
+            s->var[0] = s->var[1] = v;
+            int rc = warm_variants(s);
+            if (rc) return rc;
+        }
+        s->var[0] = keep[i].first;
+        s->var[1] = keep[i].second;
+    }
+    // the states and clocks are restored afterwards: states parked in the work buffers
+    struct Clk { double t0, dt_clock; int64_t step; };
+    std::vector<Clk> clk(n);
+    for (size_t i = 0; i < n; ++i) {
+        kd_sim* s = b->sims[i];
+        KD_CUDA(cudaStreamSynchronize(s->stream));
+        KD_CUDA(cudaMemcpyAsync(s->work, s->psi, spinor_bytes(s), cudaMemcpyDeviceToDevice, b->stream));
+        clk[i] = {s->t0, s->dt_clock, s->step};
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    KD_CUDA(cudaEventCreate(&ev[0]));
+    KD_CUDA(cudaEventCreate(&ev[1]));
+    auto timed = [&](float* ms) -> int {
+        int rc = kd_batch_step(b, dt, steps, 0, nullptr, 0, nullptr);   // captures the graphs
+        if (rc) return rc;
+        KD_CUDA(cudaEventRecord(ev[0], b->stream));
+        rc = kd_batch_step(b, dt, steps, 0, nullptr, 0, nullptr);
+        if (rc) return rc;
+        KD_CUDA(cudaEventRecord(ev[1], b->stream));
+        KD_CUDA(cudaEventSynchronize(ev[1]));
+        KD_CUDA(cudaEventElapsedTime(ms, ev[0], ev[1]));
+        return KD_OK;
+    };
+    auto set_var = [&](size_t i, int ax, int v) {
+        kd_sim* s = b->sims[i];
+        if (s->var[ax] != v) {
+            s->var[ax] = v;
+            clear_graphs(s);
+        }
+    };
+    // greedy: per axis, per group of members with the same grid and form, the variant
+    // with the shortest batch time (kept only when > 2 % faster than the group's current)
+    std::map<std::tuple<int, int, int>, std::vector<size_t>> groups;
+    for (size_t i = 0; i < n; ++i) {
+        kd_sim* s = b->sims[i];
+        if (s->prec != KD_FP64) groups[std::make_tuple(s->g.nx, s->g.ny, (int)s->tc)].push_back(i);
+    }
+    int rc = KD_OK;
+    float base = 0.0f;
+    if (!groups.empty()) rc = timed(&base);
+    for (int ax = 0; ax < 2 && !rc; ++ax)
+        for (auto& kv : groups) {
+            if (rc) break;
+            const int cur = b->sims[kv.second[0]]->var[ax];
+            int best = cur;
+            float best_ms = base;
+            for (int v = 0; v < KD_SWEEP_VARIANTS && !rc; ++v) {
+                if (v == cur) continue;
+                for (size_t i : kv.second) set_var(i, ax, v);
+                float ms = 0.0f;
+                rc = timed(&ms);
+                if (!rc && ms < 0.98f * best_ms) { best = v; best_ms = ms; }
+            }
+            for (size_t i : kv.second) set_var(i, ax, best);
+            base = best_ms;
+        }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    // states and clocks back (whatever happened above)
+    for (size_t i = 0; i < n; ++i) {
+        kd_sim* s = b->sims[i];
+        cudaMemcpyAsync(s->psi, s->work, spinor_bytes(s), cudaMemcpyDeviceToDevice, b->stream);
+        s->t0 = clk[i].t0;
+        s->dt_clock = clk[i].dt_clock;
+        s->step = clk[i].step;
+        clear_graphs(s);
+    }
+    KD_CUDA(cudaStreamSynchronize(b->stream));
+    if (rc) {
+        for (size_t i = 0; i < n; ++i) {
+            b->sims[i]->var[0] = keep[i].first;
+            b->sims[i]->var[1] = keep[i].second;
+        }
+        return rc;
+    }
+    if (variants)
+        for (size_t i = 0; i < n; ++i) {
+            variants[2 * i] = b->sims[i]->var[0];
+            variants[2 * i + 1] = b->sims[i]->var[1];
+        }
+    return KD_OK;
+}
+
 int kd_observe(kd_sim* s, const kd_obs_spec* spec, kd_obs* out) {
     int rc = check_sim(s);
     if (rc) return rc;

@@ -105,6 +105,7 @@ _SIGS = {
     "kd_batch_step": (C.c_int, [_vp, _P(C.c_double), C.c_int64, C.c_int64, _P(kd_obs), C.c_int64,
                                 _P(C.c_int64)]),
     "kd_batch_destroy": (None, [_vp]),
+    "kd_batch_autotune": (C.c_int, [_vp, _P(C.c_double), C.c_int32, _P(C.c_int32)]),
     "kd_mlp_create": (C.c_int, [_P(C.c_int32), C.c_int32, _P(_vp)]),
     "kd_mlp_num_params": (C.c_int, [_vp, _P(C.c_int64)]),
     "kd_mlp_set_params": (C.c_int, [_vp, _vp, C.c_int32]),
@@ -319,6 +320,15 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+    def autotune(self, dts, steps: int = 20) -> list:
+        """Launch variants timed on the whole batch (``kd_batch_autotune``); the members'
+        states are unchanged.  Returns [(vx, vy)] per member."""
+        n = len(self.sims)
+        dt_arr = (C.c_double * n)(*[float(d) for d in dts])
+        out = (C.c_int32 * (2 * n))()
+        _check(kd_batch_autotune(self._h, dt_arr, steps, out))
+        return [(out[2 * i], out[2 * i + 1]) for i in range(n)]
 
     def step(self, dts, nsteps: int, obs_every: int = 0):
         n = len(self.sims)

@@ -65,3 +65,36 @@ def test_batch_rejects_duplicates_and_bad_dt(kd):
         with kd.Batch([s]) as b:
             with pytest.raises(kd.KdError):
                 b.step([-1.0], 3)
+
+
+def test_batch_autotune_keeps_states_and_steps_like_members_alone(kd):
+    """kd_batch_autotune times launch variants on the whole batch and restores every
+    member's state and clock; afterwards the batch still equals its members run alone
+    with the chosen variants, bit for bit."""
+    wls = [W.small(128, 128, W.GAUSS, units=W.ATOMIC, a0=0.2), W.small(256, 128, W.GAUSS, units=W.ATOMIC),
+           W.small(128, 128, W.PLANE, units=W.ATOMIC, a0=0.3), W.small(64, 256, W.GAUSS, units=W.ATOMIC)]
+    sims = [kd.Sim.from_workload(wl.with_(precision=1)) for wl in wls]
+    before = []
+    for s, wl in zip(sims, wls):
+        s.init_packet(wl.packet)
+        s.step(wl.dt, 3)
+        before.append((s.get_spinor(), s.get_time(), s.get_state()))
+    dts = [wl.dt for wl in wls]
+    with kd.Batch(sims) as b:
+        chosen = b.autotune(dts, steps=10)
+        for s, (psi, tm, _), v in zip(sims, before, chosen):
+            assert np.array_equal(s.get_spinor(), psi)
+            assert s.get_time() == tm
+            assert s.sweep_variants == v and all(0 <= x < kd.KD_SWEEP_VARIANTS for x in v)
+        # members of the same grid and form share their variants
+        assert chosen[0] == chosen[2]
+        b.step(dts, 20)
+    batched = [s.get_spinor() for s in sims]
+    for s in sims:
+        s.close()
+    for wl, (psi, tm, blob), v, got in zip(wls, before, chosen, batched):
+        with kd.Sim.from_workload(wl.with_(precision=1)) as alone:
+            alone.sweep_variants = v
+            alone.set_state(blob)         # the member's state and clock before the batch
+            alone.step(wl.dt, 20)
+            assert np.array_equal(alone.get_spinor(), got)
