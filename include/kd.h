@@ -11,7 +11,8 @@
  *    kd_last_error() returns a thread-local message describing the last failure.
  *  - A spinor is an array of complex numbers laid out [ny][nx][4], point-major,
  *    components in the Dirac (standard) representation (psi1..psi4), complex128
- *    (interleaved doubles) for KD_FP64 simulations and complex64 for KD_FP32.
+ *    (interleaved doubles) for KD_FP64 simulations and complex64 for KD_FP32 and
+ *    KD_FP32_TC.
  *    Row iy, column ix is the point (x_min + ix dx, y_min + iy dy) of the box at t = 0.
  *  - `where` = KD_HOST for a host pointer (the call copies synchronously) or
  *    KD_DEVICE for a device pointer on the simulation's GPU (the call is ordered on the
@@ -48,9 +49,11 @@ extern "C" {
 /* Precision form: complex64 spinor and tables as KD_FP32, but the full sweeps of axes of
  * 1024 points evaluate their FFTs as 32-point DFT matrix products on the tensor cores
  * (four-step 1024 = 32 x 32 FFT of Sec. II.D's transforms; FP16 operands split hi + lo,
- * three products per term, FP32 accumulation): ~1e-7 relative per stage.  The half sweeps
- * at run ends and axes of other lengths run the KD_FP32 kernels.  State and checkpoints
- * are those of KD_FP32 (interchangeable). */
+ * three products per term, FP32 accumulation).  The tensor cores' FP32 accumulation
+ * truncates, so the norm decays by ~7e-7 per step (1.4e-3 over a 2000-step run; KD_FP32:
+ * below 1e-6) and the error against FP64 grows with it (~1e-4 after 200 steps).  The half
+ * sweeps at run ends and axes of other lengths run the KD_FP32 kernels.  State and
+ * checkpoints are those of KD_FP32 (interchangeable). */
 #define KD_FP32_TC 2
 
 #define KD_HOST 0
