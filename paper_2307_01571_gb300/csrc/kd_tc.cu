@@ -22,9 +22,11 @@
 // FP16 range: values are carried with power-of-two scales (exact) chosen per sweep from
 // the state's 2-norm, so that no operand can exceed 2^14 (bounds from the growth of the
 // unnormalised DFTs), and the DFT matrix is stored times 2^10 so that its lo parts stay
-// normal FP16 numbers.  Accuracy ~1e-7 of the line maximum per stage (vs ~6e-8 for the
-// FP32 CUDA-core stages).  Only the full sweeps (both FFTs) of N = 1024 axes run here; the
-// half sweeps at run ends and other axis lengths use the FP32 CUDA-core kernels.
+// normal FP16 numbers.  Operand rounding is ~1e-7 of the line maximum per stage (FP32
+// CUDA-core stages: ~6e-8), but the tensor cores' FP32 accumulation truncates, which
+// shrinks the norm by ~2e-7 per stage (~7e-7 per Strang step with one axis here).  Only the
+// full sweeps (both FFTs) of N = 1024 axes run here; the half sweeps at run ends and other
+// axis lengths use the FP32 CUDA-core kernels.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
