@@ -157,6 +157,24 @@ def aggregate(ms_local: float, points_per_rank: float, dist=None, device=None):
     return points_per_rank * world / (ms * 1e-3), ms
 
 
+def host_info() -> dict:
+    """Core count and CPU model of the host the oracle ran on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.machine()
+    return {"nproc": os.cpu_count(), "cpu": model}
+
+
 def oracle_rate(wl, nsteps: int):
     """The CPU oracle as it stands, single-threaded, on nsteps Strang steps of wl's grid."""
     import oracle
@@ -189,7 +207,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "grid": [wl.grid.nx, wl.grid.ny],
                    "strang_steps_per_step": per, "parallelism": "cpu oracle, 1 thread"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                          "sample": f"{per} Strang steps of the 1024x512 FP64 run per bench step"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -536,7 +554,8 @@ def main():
         if fr:
             line["error_vs_oracle"]["full_run"] = fr
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"4 Strang steps of the 1024x512 FP64 run ({dt:.1f} s)"}
+                                "sample": f"4 Strang steps of the 1024x512 FP64 run ({dt:.1f} s)",
+                                "host": host_info()}
     if dist:
         dist.barrier()
         dist.destroy_process_group()
