@@ -102,8 +102,9 @@ class Clocks:
 
     def __init__(self, dev_uuid: str | None):
         self.proc = None
-        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
-        os.makedirs(os.path.dirname(self.out), exist_ok=True)
+        import tempfile
+        fd, self.out = tempfile.mkstemp(prefix="kd_clocks_", suffix=".csv")
+        os.close(fd)
         cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
         if dev_uuid:
             cmd += ["-i", dev_uuid]
@@ -123,9 +124,12 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.fh.close()
+        with open(self.out) as fh:
+            lines = fh.readlines()
+        os.remove(self.out)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.out):
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
