@@ -111,3 +111,24 @@ def test_tc_bounded_wait_gives_up_and_context_survives(kd):
     with kd.Sim.from_workload(wl.with_(precision=1)) as s32:
         with pytest.raises(kd.KdError):
             s32.inject_fault()
+
+
+def test_tc_member_in_a_batch_matches_it_alone(kd):
+    """A KD_FP32_TC simulation advanced as one branch of a batch (its operand scales set by
+    the batch's per-member prologue) equals the same simulation run alone, bit for bit."""
+    wls = [W.small(1024, 32, W.GAUSS, units=W.ATOMIC, a0=0.3), W.small(128, 256, W.GAUSS, units=W.ATOMIC)]
+    precs = [TC, 1]
+    alone = []
+    for wl, p in zip(wls, precs):
+        with kd.Sim.from_workload(wl.with_(precision=p)) as sim:
+            sim.init_packet(wl.packet)
+            sim.step(wl.dt, 25, obs_every=5)
+            alone.append(sim.get_spinor())
+    sims = [kd.Sim.from_workload(wl.with_(precision=p)) for wl, p in zip(wls, precs)]
+    for s, wl in zip(sims, wls):
+        s.init_packet(wl.packet)
+    with kd.Batch(sims) as b:
+        b.step([wl.dt for wl in wls], 25, obs_every=5)
+    for s, a in zip(sims, alone):
+        assert np.array_equal(s.get_spinor(), a)
+        s.close()
