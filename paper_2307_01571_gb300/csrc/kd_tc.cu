@@ -36,7 +36,9 @@
 namespace kd {
 namespace tc {
 
-constexpr int N = 1024, L = 32, LC = 4, THREADS = 128;
+// 256 threads: two per accumulator row (TMEM lane), each handling half of the row's 32
+// complex columns in every phase, so that 16 warps per SM hide the latencies
+constexpr int N = 1024, L = 32, LC = 4, THREADS = 256, HALF = L / 2;
 // A operand tile of one component: 128 rows x 32 complex FP16 in the no-swizzle K-major
 // canonical layout (8-row x 16-byte core matrices); LBO = byte step between core matrices
 // along K, SBO = byte step between 8-row groups.  The padding (144 instead of 128, 1168
@@ -217,15 +219,18 @@ __global__ void __launch_bounds__(THREADS, 2) tc_sweep(const SweepArgs a) {
         uint4* dst = reinterpret_cast<uint4*>(sm + OFF_B);
         for (int i = t; i < (int)(4 * BMAT / 16); i += THREADS) dst[i] = __ldg(src + i);
     }
-    // row r = 4 vec + line: the thread's row is its TMEM lane in every stage
-    const int vec = t >> 2, ln = t & 3;
-    float2 tw[L];   // w_N^(D1 vec k) / 2^10, k < 32 (the second FFT uses the conjugates)
+    // row r = 4 vec + line: the thread's row is its TMEM lane in every stage; half h of
+    // the CTA takes columns [16 h, 16 h + 16) of it
+    const int r = t & 127, h = t >> 7;
+    const int vec = r >> 2, ln = r & 3;
+    float2 tw[HALF];   // w_N^(D1 vec k) / 2^10, k in this half (the second FFT: conjugates)
     {
         const float2* tab = reinterpret_cast<const float2*>(a.tc_tw);
 #pragma unroll
-        for (int k = 0; k < L; ++k) {
+        for (int i = 0; i < HALF; ++i) {
+            const int k = HALF * h + i;
             const float2 e = __ldg(tab + ((vec * k) & (N - 1)));
-            tw[k] = make_float2(e.x * BSCALE_INV, (float)D1 * e.y * BSCALE_INV);
+            tw[i] = make_float2(e.x * BSCALE_INV, (float)D1 * e.y * BSCALE_INV);
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(THREADS, 2) tc_sweep(const SweepArgs a) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *slot;
-    const uint32_t trow = tmem + ((uint32_t)(w * 32) << 16);   // this warp's lane quadrant
+    const uint32_t trow = tmem + ((uint32_t)((w & 3) * 32) << 16);   // this warp's lane quadrant
 
     // wait for the previous kernel in the stream (programmatic dependent launch)
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -326,10 +331,9 @@ __global__ void __launch_bounds__(THREADS, 2) tc_sweep(const SweepArgs a) {
     for (int item = blockIdx.x; item < items && !failed; item += gridDim.x) {
         const int pr = item & 1;
         const int line = (item >> 1) * LC + ln;   // this thread's line
-        const int r = t;                          // this thread's row
         // ---- load: row (vec, ln) of S1 holds x[vec + 32 q], q < 32, scaled by sa
-#pragma unroll 4
-        for (int j = 0; j < 8; ++j) {
+#pragma unroll 2
+        for (int j = 4 * h; j < 4 * h + 4; ++j) {
             uint32_t uh[4], ul[4], lh[4], ll[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -343,19 +347,19 @@ __global__ void __launch_bounds__(THREADS, 2) tc_sweep(const SweepArgs a) {
         // ---- S1, T1, transpose into S2 rows (k2, ln), column vec
         if (!stage(b1)) { failed = true; break; }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int jj = 0; jj < 2; ++jj) {
             float du[16], dl[16];
-            read8(j, du, dl);
+            read8(2 * h + jj, du, dl);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const int k2 = 8 * j + k;
-                const float2 yu = cmulf(make_float2(du[2 * k], du[2 * k + 1]), tw[k2]);
-                const float2 yl = cmulf(make_float2(dl[2 * k], dl[2 * k + 1]), tw[k2]);
-                uint32_t h, lo;
-                split(yu.x, yu.y, &h, &lo);
-                put1(0, 4 * k2 + ln, vec, h, lo);
-                split(yl.x, yl.y, &h, &lo);
-                put1(1, 4 * k2 + ln, vec, h, lo);
+                const int k2 = HALF * h + 8 * jj + k;
+                const float2 yu = cmulf(make_float2(du[2 * k], du[2 * k + 1]), tw[8 * jj + k]);
+                const float2 yl = cmulf(make_float2(dl[2 * k], dl[2 * k + 1]), tw[8 * jj + k]);
+                uint32_t hw, lw;
+                split(yu.x, yu.y, &hw, &lw);
+                put1(0, 4 * k2 + ln, vec, hw, lw);
+                split(yl.x, yl.y, &hw, &lw);
+                put1(1, 4 * k2 + ln, vec, hw, lw);
             }
         }
         // ---- S2: row (k2 = vec, ln) now holds X[vec + 32 k1]; pointwise factor in place
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(THREADS, 2) tc_sweep(const SweepArgs a) {
             const float y = ybase + (float)line * a.dy_f;
             const float y2 = y * y;
 #pragma unroll 1
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 2 * h; j < 2 * h + 2; ++j) {
                 float du[16], dl[16];
                 read8(j, du, dl);
                 uint32_t uh[4], ul[4], lh[4], ll[4];
@@ -391,26 +395,26 @@ __global__ void __launch_bounds__(THREADS, 2) tc_sweep(const SweepArgs a) {
         // ---- S3, T2 (conjugate twiddles), transpose into S4 rows (c2, ln), column vec
         if (!stage(b2)) { failed = true; break; }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int jj = 0; jj < 2; ++jj) {
             float du[16], dl[16];
-            read8(j, du, dl);
+            read8(2 * h + jj, du, dl);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const int c2 = 8 * j + k;
-                const float2 wc = make_float2(tw[c2].x, -tw[c2].y);
+                const int c2 = HALF * h + 8 * jj + k;
+                const float2 wc = make_float2(tw[8 * jj + k].x, -tw[8 * jj + k].y);
                 const float2 yu = cmulf(make_float2(du[2 * k], du[2 * k + 1]), wc);
                 const float2 yl = cmulf(make_float2(dl[2 * k], dl[2 * k + 1]), wc);
-                uint32_t h, lo;
-                split(yu.x, yu.y, &h, &lo);
-                put1(0, 4 * c2 + ln, vec, h, lo);
-                split(yl.x, yl.y, &h, &lo);
-                put1(1, 4 * c2 + ln, vec, h, lo);
+                uint32_t hw, lw;
+                split(yu.x, yu.y, &hw, &lw);
+                put1(0, 4 * c2 + ln, vec, hw, lw);
+                split(yl.x, yl.y, &hw, &lw);
+                put1(1, 4 * c2 + ln, vec, hw, lw);
             }
         }
         // ---- S4: row (c2 = vec, ln) holds Y[vec + 32 c1]; store
         if (!stage(b2)) { failed = true; break; }
 #pragma unroll 1
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 2 * h; j < 2 * h + 2; ++j) {
             float du[16], dl[16];
             read8(j, du, dl);
 #pragma unroll
