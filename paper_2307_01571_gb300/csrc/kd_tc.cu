@@ -219,10 +219,13 @@ __global__ void __launch_bounds__(THREADS, 2) tc_sweep(const SweepArgs a) {
         uint4* dst = reinterpret_cast<uint4*>(sm + OFF_B);
         for (int i = t; i < (int)(4 * BMAT / 16); i += THREADS) dst[i] = __ldg(src + i);
     }
-    // row r = 4 vec + line: the thread's row is its TMEM lane in every stage; half h of
-    // the CTA takes columns [16 h, 16 h + 16) of it
+    // the thread's row r is its TMEM lane in every stage; half h of the CTA takes columns
+    // [16 h, 16 h + 16) of it.  Row of (vector, line): x axis 32 line + vector (a warp's
+    // lanes are consecutive points of one row: contiguous loads, conflict-free transposes),
+    // y axis 4 vector + line (a warp spans 4 adjacent columns: 64-byte segments)
+    auto rowof = [](int v, int l) { return AXIS == AXIS_X ? 32 * l + v : 4 * v + l; };
     const int r = t & 127, h = t >> 7;
-    const int vec = r >> 2, ln = r & 3;
+    const int vec = AXIS == AXIS_X ? (r & 31) : (r >> 2), ln = AXIS == AXIS_X ? (r >> 5) : (r & 3);
     float2 tw[HALF];   // w_N^(D1 vec k) / 2^10, k in this half (the second FFT: conjugates)
     {
         const float2* tab = reinterpret_cast<const float2*>(a.tc_tw);
@@ -357,9 +360,9 @@ __global__ void __launch_bounds__(THREADS, 2) tc_sweep(const SweepArgs a) {
                 const float2 yl = cmulf(make_float2(dl[2 * k], dl[2 * k + 1]), tw[8 * jj + k]);
                 uint32_t hw, lw;
                 split(yu.x, yu.y, &hw, &lw);
-                put1(0, 4 * k2 + ln, vec, hw, lw);
+                put1(0, rowof(k2, ln), vec, hw, lw);
                 split(yl.x, yl.y, &hw, &lw);
-                put1(1, 4 * k2 + ln, vec, hw, lw);
+                put1(1, rowof(k2, ln), vec, hw, lw);
             }
         }
         // ---- S2: row (k2 = vec, ln) now holds X[vec + 32 k1]; pointwise factor in place
@@ -406,9 +409,9 @@ __global__ void __launch_bounds__(THREADS, 2) tc_sweep(const SweepArgs a) {
                 const float2 yl = cmulf(make_float2(dl[2 * k], dl[2 * k + 1]), wc);
                 uint32_t hw, lw;
                 split(yu.x, yu.y, &hw, &lw);
-                put1(0, 4 * c2 + ln, vec, hw, lw);
+                put1(0, rowof(c2, ln), vec, hw, lw);
                 split(yl.x, yl.y, &hw, &lw);
-                put1(1, 4 * c2 + ln, vec, hw, lw);
+                put1(1, rowof(c2, ln), vec, hw, lw);
             }
         }
         // ---- S4: row (c2 = vec, ln) holds Y[vec + 32 c1]; store
