@@ -14,10 +14,11 @@
 //   B = the real 64 x 64 form of the 32-point DFT matrix ([[c, -s], [s, c]] blocks),
 // M = 128, N = 64, K = 64, issued by one thread as 3 terms x 4 K-steps per component:
 //   A_hi B_hi + A_lo B_hi + A_hi B_lo   (hi = fp16(v), lo = fp16(v - hi): ~22 bits).
-// The products accumulate in FP32 in tensor memory; each thread reads its own row back
-// with tcgen05.ld (row r = TMEM lane r), applies the twiddle or the pointwise factor in
-// FP32 on registers and writes the next stage's operand to shared memory, transposing
-// between S1 and S2 (and S3 and S4) by its scattered stores.
+// The products accumulate in FP32 in tensor memory; two threads share each row (row r =
+// TMEM lane r, one thread per half of its columns) and read it back with tcgen05.ld, apply
+// the twiddle or the pointwise factor in FP32 on registers and write the next stage's
+// operand to shared memory, transposing between S1 and S2 (and S3 and S4) by their
+// scattered stores.
 //
 // FP16 range: values are carried with power-of-two scales (exact) chosen per sweep from
 // the state's 2-norm, so that no operand can exceed 2^14 (bounds from the growth of the
