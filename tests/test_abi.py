@@ -67,3 +67,21 @@ def test_no_cpu_fallback_without_device(kd):
     with pytest.raises(kd.KdError) as e:
         kd.Sim.from_workload(wl)
     assert e.value.code == kd.KD_ERR_CUDA
+
+
+def test_launch_variant_count_agrees_everywhere(kd):
+    """The FP32 sweep launch variants are compiled one object file per variant (build
+    script), enumerated by the internal variant table, exported as KD_SWEEP_VARIANTS in the
+    public header and mirrored by the Python binding: all four must agree."""
+    hdr = open(os.path.join(ROOT, "include", "kd.h")).read()
+    m = re.search(r"#define\s+KD_SWEEP_VARIANTS\s+(\d+)", hdr)
+    assert m
+    n = int(m.group(1))
+    internal = open(os.path.join(ROOT, "paper_2307_01571_gb300", "csrc", "kd_internal.h")).read()
+    assert re.search(rf"constexpr int kNumSweepVariants = {n};", internal)
+    # one table entry per variant and axis (the default closes each axis's chain)
+    table = internal[internal.index("sweep_variant(int axis, int v)"):internal.index("sweep_nc(")]
+    assert table.count("SweepVariant{") == 2 * n
+    assert _build.SWEEP_VARIANTS == n
+    assert kd.KD_SWEEP_VARIANTS == n
+    assert sum(1 for u in _build.UNITS if u[0] == "kd_sweep_f32.cu") == n
