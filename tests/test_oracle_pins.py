@@ -452,3 +452,89 @@ def test_packet_and_observables_against_numpy():
     dens = oracle.density_x(g, psi2)
     assert np.allclose(dens, np.sum(np.abs(psi2) ** 2, axis=(0, 2)) * (g.y_max - g.y_min) / g.ny,
                        atol=1e-15)
+
+
+# ----------------------------------------------------------------- initial packet
+# Eq. (Density_distribution_of_Gaussian_wave_packet), Sec. II.C: the momentum amplitude
+# is exp(-|pi - p0|^2 / (4 sigma_p^2)) times a position phase exp(-i r0.p / hbar), and
+# phi = u^s rho.  These pins check the packet through moments computed here with numpy
+# momenta and positions (not the oracle's): the sampled Gaussian |rho|^2 on a grid with
+# dp = sigma_p / 2 has mean p0 and standard deviation sigma_p up to Poisson-summation
+# terms of order exp(-2 pi^2 sigma_p^2 / dp^2) = e^-79.
+def _moment_grid(n=64, sig=0.02, frac_x=0.3, frac_y=0.45):
+    dp = sig / 2
+    L = 2 * math.pi / dp
+    return W.Grid(n, n, -frac_x * L, (1 - frac_x) * L, -frac_y * L, (1 - frac_y) * L), L, dp
+
+
+def _axis_momenta(g, f):
+    px = 2 * np.pi * np.fft.fftfreq(g.nx, d=(g.x_max - g.x_min) / g.nx) + f.p_shift_x
+    py = 2 * np.pi * np.fft.fftfreq(g.ny, d=(g.y_max - g.y_min) / g.ny) + f.p_shift_y
+    return px, py
+
+
+@pytest.mark.parametrize("spin", [1, -1])
+@pytest.mark.parametrize("basis", [0, 1])
+def test_packet_momentum_mean_and_width(spin, basis):
+    sig = 0.02
+    g, L, dp = _moment_grid(sig=sig)
+    f = W.Field(kind=W.NONE, p_shift_x=0.013, p_shift_y=0.7)
+    # p0 off the grid points on both axes, kinetic (pi = p + p_shift)
+    pk = W.Packet(0.013 + 3.3 * dp, 0.7 - 5.6 * dp, 0.1 * L, -0.2 * L, sig, spin, basis)
+    psi = oracle.init_packet(NAT, g, f, pk)
+    md = oracle.momentum_density(NAT, g, f, psi, basis=basis)
+    px, py = _axis_momenta(g, f)
+    w = md[:, :, 0] / md[:, :, 0].sum()
+    wx, wy = w.sum(0), w.sum(1)
+    mx, my = (wx * px).sum(), (wy * py).sum()
+    sx = math.sqrt((wx * (px - mx) ** 2).sum())
+    sy = math.sqrt((wy * (py - my) ** 2).sum())
+    assert abs(mx - pk.p0x) < 1e-12 and abs(my - pk.p0y) < 1e-12
+    assert abs(sx / sig - 1) < 1e-10 and abs(sy / sig - 1) < 1e-10
+    # the amplitude itself is the sampled Gaussian, cell by cell
+    gauss = np.exp(-((py[:, None] - pk.p0y) ** 2 + (px[None, :] - pk.p0x) ** 2) / (2 * sig ** 2))
+    assert np.max(np.abs(w - gauss / gauss.sum())) < 1e-13
+    # a pure u^s packet: all of |phi|^2 is in the spin-s projection, none in the other
+    mine, other = (1, 2) if spin == 1 else (2, 1)
+    assert np.max(np.abs(md[:, :, mine] - md[:, :, 0])) < 1e-14 * md[:, :, 0].max()
+    assert md[:, :, other].max() < 1e-26
+
+
+@pytest.mark.parametrize("spin,basis", [(1, 0), (-1, 0), (1, 1), (-1, 1)])
+@pytest.mark.parametrize("fx,fy", [(0.5, 0.5), (0.3, 0.45)])
+def test_packet_position_centre(spin, basis, fx, fy):
+    """With p0 = 0 and no momentum shift, u^s(-p) = beta u^s(p), so |psi|^2 is exactly
+    symmetric about r0: its mean is r0, on a centred and on an off-centre box."""
+    sig = 0.02
+    g, L, dp = _moment_grid(sig=sig, frac_x=fx, frac_y=fy)
+    f = W.Field(kind=W.NONE)
+    dx = L / g.nx
+    r0x, r0y = g.x_min + 29 * dx, g.y_min + 35 * dx
+    pk = W.Packet(0.0, 0.0, r0x, r0y, sig, spin, basis)
+    psi = oracle.init_packet(NAT, g, f, pk)
+    dens = np.sum(np.abs(psi) ** 2, axis=2)
+    x = g.x_min + np.arange(g.nx) * dx
+    y = g.y_min + np.arange(g.ny) * dx
+    w = dens / dens.sum()
+    assert abs((w.sum(0) * x).sum() - r0x) < 1e-9 * L
+    assert abs((w.sum(1) * y).sum() - r0y) < 1e-9 * L
+    # spatial width hbar / (2 sigma_p) per axis of the scalar Gaussian (the spinor
+    # structure adds a relative correction of order (sigma_p / m c)^2)
+    sx = math.sqrt((w.sum(0) * (x - r0x) ** 2).sum())
+    assert abs(sx / (1.0 / (2 * sig)) - 1) < 1e-3
+
+
+def test_packet_position_phase_translates_exactly():
+    """Moving r0 by whole grid cells (mx, my) moves the state by exactly that cyclic shift:
+    the position phase exp(-i r0.p/hbar) with the grid's own momenta is a discrete
+    translation.  A wrong sign or scale of the phase breaks this."""
+    sig = 0.02
+    g, L, dp = _moment_grid(sig=sig)
+    f = W.Field(kind=W.NONE, p_shift_x=0.01, p_shift_y=0.5)
+    dx = L / g.nx
+    a = W.Packet(0.01 + 2.2 * dp, 0.5 - 1.7 * dp, 0.05 * L, 0.1 * L, sig, 1, 0)
+    mx, my = 7, -5
+    b = W.Packet(a.p0x, a.p0y, a.r0x + mx * dx, a.r0y + my * dx, sig, 1, 0)
+    pa = oracle.init_packet(NAT, g, f, a)
+    pb = oracle.init_packet(NAT, g, f, b)
+    assert np.max(np.abs(pb - np.roll(pa, (my, mx), axis=(0, 1)))) < 1e-12 * np.max(np.abs(pa))
