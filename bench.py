@@ -53,6 +53,12 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-surrogate", action="store_true")
     p.add_argument("--no-tc", action="store_true", help="skip the tensor-core precision form")
+    p.add_argument("--no-hbm", action="store_true", help="skip the HBM-resident 4096x2048 grid")
+    p.add_argument("--profile-sweep", default=None, metavar="PREC,KIND,REPS[,GRID]",
+                   help="profiling mode: build the GRID workload (1024x512 default, or 4096x2048), "
+                        "step it twice, then run REPS back-to-back sweeps of KIND (0 x, 1 y) at "
+                        "precision PREC (0 FP64, 1 FP32, 2 tensor-core form) on the default "
+                        "launch variants, and exit")
     p.add_argument("--sweep-variants", default=None,
                    help="X,Y: launch variants of the FP32 sweeps instead of the autotuner's choice "
                         "(a profiler distorts the tuner's timings)")
@@ -374,8 +380,74 @@ def surrogate_form(n_runs: int = 4096):
             "constant_predictor_rms_log10": {k: v["rms"] for k, v in base.items()}}
 
 
+def profile_sweep(spec: str):
+    """Runs a few fused sweeps in isolation for a profiler.  The simulation is created (one
+    warm-up launch of every sweep shape), initialised with the workload's packet and
+    advanced 2 Strang steps; then kd_bench_sweep(KIND, REPS) runs REPS back-to-back full
+    sweeps (for the FP32/FP64 sweep kernels, ncu -k regex:sweep_kernel, the benchmarked
+    launches are numbers 14 .. 13 + REPS; for the tensor-core kernel, -k regex:tc_sweep,
+    numbers 3 .. 2 + REPS)."""
+    from paper_2307_01571_gb300 import kd
+    f = spec.split(",")
+    prec, kind, reps = int(f[0]), int(f[1]), int(f[2])
+    grid = f[3] if len(f) > 3 else "1024x512"
+    wl = {"1024x512": W.c2, "2048x1024": W.c3, "4096x2048": W.hbm}[grid](precision=prec, nsteps=2)
+    with kd.Sim.from_workload(wl) as sim:
+        sim.init_packet(wl.packet)
+        sim.step(wl.dt, 2)
+        sim.bench_sweep(kind, reps)
+        sim.get_time()
+    print("ok", prec, kind, reps, grid)
+
+
+def hbm_resident(kd, stream, hbm_peak, hbm_src, flush, tuned):
+    """FP32 step on a grid whose state does not fit in L2 (4096x2048, 256 MiB spinor plus
+    a 64 MiB kinetic table): 200 Strang steps with observations every 100, and each sweep
+    timed alone (back-to-back launches), with the roofline of the slower sweep."""
+    import torch
+    wl = W.hbm(precision=W.FP32)
+    sim = kd.Sim.from_workload(wl, stream=stream.cuda_stream)
+    sim.init_packet(wl.packet)
+    tune = tuned(sim, wl.dt)
+    sim.step(wl.dt, wl.nsteps, obs_every=wl.obs_every)          # warm-up (graphs captured)
+    sim.init_packet(wl.packet)
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(wl.dt, wl.nsteps, obs_every=wl.obs_every)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    sweep = {}
+    for kind, nm in ((0, "x_sweep"), (1, "y_sweep")):
+        sim.bench_sweep(kind, 20)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.bench_sweep(kind, 20)
+        b.record(stream)
+        b.synchronize()
+        sweep[nm] = a.elapsed_time(b) / 20
+    sim.close()
+    kern = max(sweep, key=sweep.get)
+    byts = BYTES_PER_PT_SWEEP["fp32"] * wl.points
+    ach = byts / (sweep[kern] * 1e-3) / 1e9
+    return {"workload": wl.name, "grid": [wl.grid.nx, wl.grid.ny], "dtype": "f32",
+            "value": wl.points * wl.nsteps / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms,
+            "sweep_variants": tune["variants"],
+            "roofline": {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": hbm_peak,
+                         "peak_source": hbm_src, "unit": "GB/s", "frac": ach / hbm_peak,
+                         "traffic": ncu_traffic(f"{kern}_4096x2048", "fp32"),
+                         "algorithmic_bytes_per_launch": byts,
+                         "launch_ms": {k: round(v, 5) for k, v in sweep.items()}},
+            "l2": "state 320 MiB > 129 MiB L2: every sweep streams from HBM"}
+
+
 def main():
     args = parse()
+    if args.profile_sweep:
+        return profile_sweep(args.profile_sweep)
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -528,8 +600,12 @@ def main():
     if rank == 0 and not args.no_tc:
         line["precision_form"] = precision_form(kd, stream, not args.no_cpu)
         if "fp64" in line:
-            line["precision_form"]["speedup_tc_vs_fp64_single"] = (
+            # rates per grid-point-step of different grids: the precision form on 2048x1024,
+            # the FP64 step on 1024x512
+            line["precision_form"]["speedup_tc_2048x1024_vs_fp64_1024x512"] = (
                 line["precision_form"]["tc"]["value"] / line["fp64"]["value"])
+    if rank == 0 and not args.no_hbm:
+        line["hbm_resident"] = hbm_resident(kd, stream, hbm, hbm_src, flush, tuned)
     if not args.no_batch:
         line["batched"] = batched_form(kd, stream, max(1, min(K, 3)), barrier, dist)
         if "fp64" in line:

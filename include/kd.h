@@ -43,6 +43,7 @@ extern "C" {
 #define KD_ERR_TIMEOUT (-6)          /* a bounded device wait ran out */
 #define KD_ERR_STATE_MISMATCH (-7)   /* checkpoint does not match this simulation */
 #define KD_ERR_NOMEM (-8)            /* device allocation failed */
+#define KD_ERR_CANCELLED (-9)        /* kd_step stopped early at a kd_cancel request */
 
 #define KD_FP64 0 /* complex128 spinor, FP64 arithmetic throughout */
 #define KD_FP32 1 /* complex64 spinor, FP32 arithmetic; FP64-built phase tables */
@@ -156,7 +157,15 @@ int kd_get_time(kd_sim* sim, double* t, int64_t* steps_done);
  * receives how many were produced.  Returns KD_ERR_NONFINITE if a recorded norm was not
  * finite and KD_ERR_NORM_DRIFT if one left the watchdog tolerance (the state is then
  * the state after all nsteps).  On return the state is in position space at t + nsteps dt
- * and, when obs_every > 0, the call has synchronised the stream. */
+ * and, when obs_every > 0, the call has synchronised the stream.
+ * The steps are enqueued in chunks of obs_every steps (64 without observations), each a
+ * CUDA graph launch; unless the stream is being captured, the host keeps at most four
+ * chunks in flight (it waits for the chunk four back before enqueuing the next), so the
+ * call returns when all but the last few chunks have run.
+ * Cancellation (kd_cancel): a request seen before a chunk is enqueued makes that chunk the
+ * call's last one, closed at its end, and kd_step returns KD_ERR_CANCELLED with the state
+ * a valid position-space state after the steps that ran (kd_get_time reports them, and
+ * the observation records of those steps are delivered). */
 int kd_step(kd_sim* sim, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs_out,
             int64_t obs_cap, int64_t* n_obs);
 
@@ -271,7 +280,8 @@ int kd_set_sweep_variants(kd_sim* sim, int32_t variant_x, int32_t variant_y);
 int kd_get_sweep_variants(kd_sim* sim, int32_t* variant_x, int32_t* variant_y);
 
 /* Test hook for the tensor-core sweeps' bounded waits.  kind KD_FAULT_TC_WAIT: during
- * the next kd_step call the tensor-core sweeps issue no matrix products, so every wait
+ * the next step call (kd_step, or kd_batch_step of a batch holding the simulation) the
+ * tensor-core sweeps issue no matrix products, so every wait
  * for them gives up after its iteration limit (about a second); the kernels then skip
  * their remaining work, free their tensor memory and set the simulation's status, and
  * kd_step returns KD_ERR_TIMEOUT with the context intact; the state is then not a valid
@@ -280,19 +290,33 @@ int kd_get_sweep_variants(kd_sim* sim, int32_t* variant_x, int32_t* variant_y);
 #define KD_FAULT_TC_WAIT 1
 int kd_inject_fault(kd_sim* sim, int32_t kind);
 
+/* Requests that the kd_step running on this simulation (in another host thread), or the
+ * next one, stop at its next chunk boundary (see kd_step).  The request is consumed by
+ * the kd_step that honours it.  Safe to call from any thread while kd_step runs; not
+ * applied by kd_batch_step. */
+int kd_cancel(kd_sim* sim);
+
+/* Test hook for out-of-memory handling, process-wide: with after >= 0, the device
+ * allocation made after `after` further successful ones fails as if the device were out
+ * of memory (the call that needed it returns KD_ERR_NOMEM and releases what it
+ * allocated), and the hook turns itself off; -1 turns it off.  KD_ERR_ARG for after < -1. */
+int kd_inject_alloc_failure(int32_t after);
+
 /* Number of kernel launches this simulation has enqueued so far (graph replays counted
  * node by node). */
 int kd_get_launch_count(kd_sim* sim, int64_t* launches);
 
-/* Allocation-free density read-out (no counterpart in the paper; the paper's
- * Eqs. probability_density and y_integrated_probability_density define the values).
+/* Allocation-free density read-out.  The paper has no counterpart: this is a service
+ * of the library.  It computes the norm sum |psi|^2 dx dy and the y-integrated density
+ * Phi(x) = sum_y |psi|^2 dy of a caller's device spinor.
  *
- * For callers that cannot allocate device memory: code running while a stream is being
- * captured into a CUDA graph (allocation calls are not permitted there), real-time loops
- * that must never block on the allocator, and hosts that hand the library a fixed memory
- * budget.  It needs no kd_sim and calls no cudaMalloc/cudaFree: its only scratch is a
- * static device array of KD_NOALLOC_MAX_ROWS doubles (32 KiB) that every GPU which loads
- * the library holds until the process exits.
+ * For callers that cannot allocate device memory: hosts that hand the library a fixed
+ * memory budget (another framework's pool already owns the device memory), real-time
+ * loops that must never wait on the allocator (cudaMalloc and cudaFree can synchronise
+ * the device), and plug-ins running inside a runtime that forbids them to allocate.  It
+ * needs no kd_sim and calls no cudaMalloc/cudaFree: its only scratch is a static device
+ * array of KD_NOALLOC_MAX_ROWS doubles (32 KiB) that every GPU which loads the library
+ * holds until the process exits.
  *
  *  psi            device pointer, [ny][nx][4] complex spinor in the layout above,
  *                 complex128 (KD_FP64) or complex64 (KD_FP32); caller-owned
@@ -300,13 +324,16 @@ int kd_get_launch_count(kd_sim* sim, int64_t* launches);
  *  norm_out       device pointer to one double: sum |psi|^2 dx dy (may be NULL)
  *  density_x_out  device pointer to nx doubles: Phi(x) = sum_y |psi|^2 dy (may be NULL)
  *  cuda_stream    cudaStream_t the work is ordered on (NULL = legacy default stream)
- * Returns KD_ERR_UNSUPPORTED_SIZE if ny > KD_NOALLOC_MAX_ROWS or nx > 4096, KD_ERR_ARG for
- * null pointers, KD_ERR_CUDA on launch failure.  Asynchronous on the stream.
+ * Both sums accumulate in FP64.  Returns KD_ERR_UNSUPPORTED_SIZE if ny >
+ * KD_NOALLOC_MAX_ROWS or nx > 4096, KD_ERR_ARG for null pointers, KD_ERR_CUDA on launch
+ * failure or without a usable device.  Asynchronous on the stream.
  *
  * The first call on each device looks up the scratch array's device address with that
- * device current; make that first call before any stream capture.  All calls on a device
- * share the one scratch array (each call overwrites every entry it reads, so nothing needs
- * clearing): calls whose kernels can overlap on the GPU (different streams without
+ * device current, and so does the first call after the device's context was replaced
+ * (cudaDeviceReset); such a call made on a stream that is being captured returns
+ * KD_ERR_CUDA, so make the first call before any stream capture.  All calls on a device
+ * share the one scratch array (each call overwrites every entry it reads, so nothing
+ * needs clearing): calls whose kernels can overlap on the GPU (different streams without
  * ordering) race on it and must be serialised by the caller. */
 #define KD_NOALLOC_MAX_ROWS 4096
 int kd_density_noalloc(const void* psi, int32_t nx, int32_t ny, int32_t precision, double dx,

@@ -14,6 +14,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -72,7 +73,30 @@ struct GraphKey {
 namespace kd {
 // Records a message for kd_last_error() from another translation unit.
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+// Clears the message of kd_last_error() after a successful call in another unit.
+void clear_error() { g_err.clear(); }
 }  // namespace kd
+
+namespace {
+// Test hook of kd_inject_alloc_failure: -1 = off; k >= 0 = the allocation after k more
+// successful ones fails as if the device were out of memory (then the hook turns off).
+std::atomic<int> g_alloc_fail_after{-1};
+
+// Every device allocation of the library goes through here.
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    int k = g_alloc_fail_after.load();
+    while (k >= 0) {
+        if (g_alloc_fail_after.compare_exchange_weak(k, k == 0 ? -1 : k - 1)) {
+            if (k == 0) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+}  // namespace
 
 struct kd_sim {
     kd_units u;
@@ -109,6 +133,11 @@ struct kd_sim {
     void* tc_tw = nullptr;
     float* tc_scale = nullptr;
     int tc_fault = 0;          // kd_inject_fault: applies to the next kd_step call only
+    std::atomic<int> cancel{0};  // kd_cancel: the running or next kd_step stops early
+    // kd_step keeps at most kRunAhead chunks in flight (host waits on the event of the
+    // chunk kRunAhead back), so that a cancellation stops work that is not yet queued
+    static constexpr int kRunAhead = 4;
+    cudaEvent_t ahead[kRunAhead] = {};
     // host clock: t = t0 + step * dt_clock
     double t0 = 0.0, dt_clock = 0.0;
     int64_t step = 0;
@@ -882,7 +911,7 @@ int rowsum_launch(kd_sim* s, const void* psi) {
 }
 
 int ensure_md(kd_sim* s) {
-    if (!s->md) KD_CUDA(cudaMalloc(&s->md, s->P * 3 * sizeof(double)));
+    if (!s->md) KD_CUDA(dev_alloc((void**)&s->md, s->P * 3 * sizeof(double)));
     return KD_OK;
 }
 
@@ -981,9 +1010,10 @@ int ensure_steps(kd_sim* s, int64_t n) {
     clear_graphs(s);
     if (s->steps) cudaFree(s->steps);
     s->steps = nullptr;
+    s->steps_cap = 0;   // no buffer until the allocation below succeeds
     int64_t cap = 1024;
     while (cap < n + 1) cap *= 2;
-    KD_CUDA(cudaMalloc(&s->steps, cap * sizeof(StepScalars)));
+    KD_CUDA(dev_alloc((void**)&s->steps, cap * sizeof(StepScalars)));
     s->steps_cap = cap;
     return KD_OK;
 }
@@ -993,9 +1023,10 @@ int ensure_obs(kd_sim* s, int64_t n) {
     clear_graphs(s);
     if (s->obs_dev) cudaFree(s->obs_dev);
     s->obs_dev = nullptr;
+    s->obs_dev_cap = 0;   // no buffer until the allocation below succeeds
     int64_t cap = 16;
     while (cap < n) cap *= 2;
-    KD_CUDA(cudaMalloc(&s->obs_dev, cap * sizeof(kd_obs)));
+    KD_CUDA(dev_alloc((void**)&s->obs_dev, cap * sizeof(kd_obs)));
     s->obs_dev_cap = cap;
     return KD_OK;
 }
@@ -1176,12 +1207,15 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
     auto bail = [&](int rc) { kd_destroy(s); return rc; };
 #define KD_ALLOC(ptr, bytes)                                                             \
     do {                                                                                 \
-        cudaError_t ea_ = cudaMalloc((void**)&(ptr), (bytes));                           \
+        cudaError_t ea_ = dev_alloc((void**)&(ptr), (bytes));                            \
         if (ea_ != cudaSuccess)                                                          \
             return bail(fail(KD_ERR_NOMEM, "cudaMalloc(%zu): %s", (size_t)(bytes), cudaGetErrorString(ea_))); \
     } while (0)
     if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(KD_ERR_CUDA, "stream create failed"));
+    for (cudaEvent_t& ev : s->ahead)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(KD_ERR_CUDA, "event create failed"));
     KD_ALLOC(s->psi, spinor_bytes(s));
     KD_ALLOC(s->work, spinor_bytes(s));
     for (int le = 0; le < 2; ++le) {
@@ -1230,6 +1264,8 @@ void kd_destroy(kd_sim* s) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    for (cudaEvent_t ev : s->ahead)
+        if (ev) cudaEventDestroy(ev);
     delete s;
 }
 
@@ -1436,14 +1472,21 @@ int enqueue_prologue(kd_sim* s, const StepPlan& p) {
 }
 
 // The chunks of a call: chunk i covers steps [i c, (i + 1) c) with c = obs_every (or 64
-// without observations); fn(chunk, last, obs) enqueues or launches one chunk.
-template <typename F> int for_each_chunk(const StepPlan& p, F fn) {
+// without observations); fn(chunk, last, obs) enqueues or launches one chunk.  When
+// *cancel is set (kd_cancel) before a chunk is enqueued, that chunk is enqueued as the
+// call's last one (it closes the state at its end boundary) and the loop stops; *done
+// receives the steps enqueued.
+template <typename F> int for_each_chunk(const StepPlan& p, F fn, std::atomic<int>* cancel = nullptr,
+                                         int64_t* done_out = nullptr) {
     const int64_t chunk_n = p.obs_every > 0 ? p.obs_every : 64;
     int64_t done = 0;
+    if (done_out) *done_out = 0;
     while (done < p.nsteps) {
+        const bool stop = cancel && cancel->exchange(0) != 0;
         const int64_t left = p.nsteps - done;
-        const int64_t chunk = left < chunk_n ? left : chunk_n;
-        const bool last = done + chunk == p.nsteps;
+        int64_t chunk = left < chunk_n ? left : chunk_n;
+        if (stop && chunk > 64 && p.obs_every == 0) chunk = 64;
+        const bool last = stop || done + chunk == p.nsteps;
         const bool obs = p.obs_every > 0 && chunk == p.obs_every;
         int rc = KD_OK;
         if (chunk <= 4096) {
@@ -1458,6 +1501,8 @@ template <typename F> int for_each_chunk(const StepPlan& p, F fn) {
         }
         if (rc) return rc;
         done += chunk;
+        if (done_out) *done_out = done;
+        if (stop) return KD_ERR_CANCELLED;
     }
     return KD_OK;
 }
@@ -1465,7 +1510,7 @@ template <typename F> int for_each_chunk(const StepPlan& p, F fn) {
 // After the loop: copy the observation records (synchronises the stream) and turn the
 // watchdog status into a return code.
 int finish_step(kd_sim* s, const StepPlan& p, kd_obs* obs_out, int64_t* n_obs) {
-    s->step += p.nsteps;
+    s->step += p.nsteps;   // the steps enqueued (fewer than asked after a cancellation)
     if (p.nobs > 0 || s->tc) {
         if (p.nobs > 0 && p.cap > 0)
             KD_CUDA(cudaMemcpyAsync(obs_out, s->obs_dev, p.cap * sizeof(kd_obs), cudaMemcpyDeviceToHost, s->stream));
@@ -1495,11 +1540,29 @@ int kd_step(kd_sim* s, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs
     if (rc || nsteps == 0) return rc;
     rc = enqueue_prologue(s, p);
     if (rc) return rc;
+    int64_t done = 0, ci = 0;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool throttle = cudaStreamIsCapturing(s->stream, &cs) == cudaSuccess &&
+                          cs == cudaStreamCaptureStatusNone;
     rc = for_each_chunk(p, [&](int chunk, bool last, bool obs) {
-        return run_chunk(s, p.dt, chunk, last, obs, p.w, p.obs_every, p.cap);
-    });
-    if (rc) return rc;
+        cudaEvent_t& ev = s->ahead[ci % kd_sim::kRunAhead];
+        if (throttle && ci >= kd_sim::kRunAhead) KD_CUDA(cudaEventSynchronize(ev));
+        int r = run_chunk(s, p.dt, chunk, last, obs, p.w, p.obs_every, p.cap);
+        if (r) return r;
+        if (throttle) KD_CUDA(cudaEventRecord(ev, s->stream));
+        ++ci;
+        return KD_OK;
+    }, &s->cancel, &done);
+    const bool cancelled = rc == KD_ERR_CANCELLED;
+    if (rc && !cancelled) return rc;
+    if (cancelled) {   // the state is closed at step `done`: account for what ran
+        p.nsteps = done;
+        p.nobs = p.obs_every > 0 ? done / p.obs_every : 0;
+        if (p.cap > p.nobs) p.cap = p.nobs;
+    }
     rc = finish_step(s, p, obs_out, n_obs);
+    if (cancelled && rc == KD_OK)
+        rc = fail(KD_ERR_CANCELLED, "kd_step cancelled after %lld of the requested steps", (long long)done);
     if (s->tc_fault) {   // an injected fault lasts one call (finish_step has synchronised)
         s->tc_fault = 0;
         clear_graphs(s);
@@ -1514,6 +1577,18 @@ int kd_inject_fault(kd_sim* s, int32_t kind) {
     if (kind == KD_FAULT_TC_WAIT && !s->tc) return fail(KD_ERR_ARG, "not a KD_FP32_TC simulation");
     s->tc_fault = kind == KD_FAULT_TC_WAIT;
     clear_graphs(s);
+    return KD_OK;
+}
+
+int kd_cancel(kd_sim* s) {
+    if (!s) return fail(KD_ERR_ARG, "null simulation");
+    s->cancel.store(1);
+    return KD_OK;
+}
+
+int kd_inject_alloc_failure(int32_t after) {
+    if (after < -1) return fail(KD_ERR_ARG, "after must be >= -1");
+    g_alloc_fail_after.store(after);
     return KD_OK;
 }
 
@@ -1663,6 +1738,10 @@ int kd_batch_step(kd_batch* b, const double* dt, int64_t nsteps, int64_t obs_eve
         int r = finish_step(s, plans[i], obs_out ? obs_out + i * (size_t)obs_cap : nullptr, n_obs);
         s->stream = saved;
         if (r && !first_err) first_err = r;
+        if (s->tc_fault) {   // an injected fault lasts one step call, batched or not
+            s->tc_fault = 0;
+            clear_graphs(s);
+        }
     }
     return first_err;
 }

@@ -1,12 +1,15 @@
 // kd_noalloc.cu -- kd_density_noalloc: position-space norm and y-integrated density of a
 // caller's spinor, for callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being captured
-// into a CUDA graph (allocation calls are not permitted there), real-time loops that must
-// not block on the allocator, and hosts that give the library a fixed memory budget.  This
-// entry point needs no kd_sim (which owns allocated buffers): its only scratch, the
-// per-row partial sums of the norm, lives in the file-scope device array below, which
-// every GPU that loads the library holds until the process exits.
+// Some callers cannot call cudaMalloc: hosts that hand the library a fixed memory budget
+// (another framework's pool already owns the device memory), real-time loops that must
+// never wait on the allocator (cudaMalloc and cudaFree can synchronise the device), and
+// plug-ins that run inside a runtime which forbids them to allocate.  This entry point
+// needs no kd_sim (which owns allocated buffers): its only scratch, the per-row partial
+// sums of the norm, lives in the file-scope device array below, which every GPU that
+// loads the library holds until the process exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -17,6 +20,7 @@
 
 namespace kd {
 int set_error(int code, const char* msg);  // kd_api.cu: message for kd_last_error()
+void clear_error();                         // kd_api.cu: kd_last_error() becomes ""
 }
 
 namespace {
@@ -25,10 +29,33 @@ namespace {
 constexpr int kMaxRows = KD_NOALLOC_MAX_ROWS;
 static __device__ __align__(256) double g_row_scratch[kMaxRows];
 
-// Device address of g_row_scratch per device ordinal, looked up once per device.
+// Device address of g_row_scratch per device ordinal, looked up once per device and
+// context: the unique id of the context the address was taken in is kept beside it, so
+// that a new primary context on that device (after cudaDeviceReset) is noticed and the
+// address looked up again instead of being used stale.
 constexpr int kMaxDevices = 64;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
 std::mutex g_setup_mu;
+
+// The two driver calls that identify the current context, found through the runtime
+// (the library links no driver library of its own, so it also loads where none exists).
+PFN_cuCtxGetCurrent_v4000 p_ctx_get_current = nullptr;
+PFN_cuCtxGetId_v12000 p_ctx_get_id = nullptr;
+
+bool driver_calls() {
+    if (p_ctx_get_current && p_ctx_get_id) return true;
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 4000, cudaEnableDefault, &qa) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+        return false;
+    p_ctx_get_current = (PFN_cuCtxGetCurrent_v4000)a;
+    p_ctx_get_id = (PFN_cuCtxGetId_v12000)b;
+    return true;
+}
 
 // Sum of |psi|^2 over one row of a [ny][nx][4] complex spinor, fixed-order tree.
 template <typename T>
@@ -94,21 +121,46 @@ extern "C" int kd_density_noalloc(const void* psi, int32_t nx, int32_t ny, int32
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return noalloc_fail(KD_ERR_CUDA, "kd_density_noalloc: no usable current CUDA device");
+    CUcontext ctx = nullptr;
+    unsigned long long ctx_id = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_setup_mu);
+        if (!driver_calls())
+            return noalloc_fail(KD_ERR_CUDA, "kd_density_noalloc: the CUDA driver's context calls are unavailable");
+    }
+    if (p_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) {
+        // this thread has not used the runtime yet: setting the current device again
+        // initialises the driver and the device's primary context (allocating nothing)
+        if (cudaSetDevice(dev) != cudaSuccess || p_ctx_get_current(&ctx) != CUDA_SUCCESS)
+            return noalloc_fail(KD_ERR_CUDA, "kd_density_noalloc: the device's context is not usable");
+    }
+    if (!ctx || p_ctx_get_id(ctx, &ctx_id) != CUDA_SUCCESS)
+        return noalloc_fail(KD_ERR_CUDA, "kd_density_noalloc: no current CUDA context");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
     double* rows = nullptr;
     {
-        // once per device, with that device current: the host-side name g_row_scratch is
-        // only a stand-in, the kernels need the device address
+        // once per device (and again after the device's context was replaced), with that
+        // device current: the host-side name g_row_scratch is only a stand-in, the
+        // kernels need the device address
         std::lock_guard<std::mutex> lk(g_setup_mu);
-        if (!g_scratch_addr[dev]) {
+        if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx_id) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+                return noalloc_fail(KD_ERR_CUDA,
+                                    "kd_density_noalloc: the first call on a device (or after its "
+                                    "context was reset) must not be made on a capturing stream");
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_row_scratch);
             if (e != cudaSuccess || !p)
                 return noalloc_fail(KD_ERR_CUDA, "kd_density_noalloc: cudaGetSymbolAddress failed");
             g_scratch_addr[dev] = (double*)p;
+            g_scratch_ctx[dev] = ctx_id;
         }
         rows = g_scratch_addr[dev];
     }
-    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // drop an earlier launch error of unrelated work on this thread, so that the check
+    // after our launches reports only our own
+    (void)cudaGetLastError();
     if (norm_out) {
         // every row of the scratch that k_sum_rows reads is written first, so nothing
         // needs clearing between calls
@@ -121,6 +173,8 @@ extern "C" int kd_density_noalloc(const void* psi, int32_t nx, int32_t ny, int32
         if (precision == KD_FP64) k_col_density<double><<<blocks, 128, 0, s>>>((const double*)psi, nx, ny, dy, density_x_out);
         else k_col_density<float><<<blocks, 128, 0, s>>>((const float*)psi, nx, ny, dy, density_x_out);
     }
-    if (cudaGetLastError() != cudaSuccess) return noalloc_fail(KD_ERR_CUDA, "kd_density_noalloc: launch failed");
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(KD_ERR_CUDA, cudaGetErrorString(e));
+    kd::clear_error();
     return KD_OK;
 }

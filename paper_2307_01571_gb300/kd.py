@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libkd.so")
 KD_OK = 0
 KD_ERR_ARG, KD_ERR_UNSUPPORTED_SIZE, KD_ERR_CUDA = -1, -2, -3
 KD_ERR_NONFINITE, KD_ERR_NORM_DRIFT, KD_ERR_TIMEOUT = -4, -5, -6
-KD_ERR_STATE_MISMATCH, KD_ERR_NOMEM = -7, -8
+KD_ERR_STATE_MISMATCH, KD_ERR_NOMEM, KD_ERR_CANCELLED = -7, -8, -9
 KD_FP64, KD_FP32, KD_FP32_TC = 0, 1, 2
 KD_HOST, KD_DEVICE = 0, 1
 KD_SWEEP_VARIANTS, KD_TUNE_FORCE = 4, 1
@@ -32,6 +32,15 @@ class KdError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"kd error {code}: {msg}")
         self.code = code
+
+
+class KdCancelled(KdError):
+    """kd_step stopped early at a kd_cancel request; ``obs`` holds the records of the
+    steps that ran."""
+
+    def __init__(self, code: int, msg: str, obs: list):
+        super().__init__(code, msg)
+        self.obs = obs
 
 
 class kd_units(C.Structure):
@@ -98,6 +107,8 @@ _SIGS = {
                               _P(C.c_float)]),
     "kd_set_sweep_variants": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "kd_inject_fault": (C.c_int, [_vp, C.c_int32]),
+    "kd_cancel": (C.c_int, [_vp]),
+    "kd_inject_alloc_failure": (C.c_int, [C.c_int32]),
     "kd_get_sweep_variants": (C.c_int, [_vp, _P(C.c_int32), _P(C.c_int32)]),
     "kd_density_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                      C.c_double, _vp, _vp, _vp]),
@@ -130,6 +141,12 @@ EXPORTS = list(_SIGS)
 def _check(rc: int):
     if rc != KD_OK:
         raise KdError(rc, kd_last_error().decode())
+
+
+def inject_alloc_failure(after: int):
+    """Test hook (``kd_inject_alloc_failure``): the device allocation after ``after``
+    further successful ones fails as if the device were out of memory; -1 turns it off."""
+    _check(kd_inject_alloc_failure(after))
 
 
 def _fill(cls, obj):
@@ -224,9 +241,17 @@ class Sim:
         cap = nobs if obs_cap is None else obs_cap
         buf = (kd_obs * max(cap, 1))()
         n = C.c_int64()
-        _check(kd_step(self._h, dt, nsteps, obs_every, buf if cap > 0 else None, cap,
-                       C.byref(n)))
-        return [{k: getattr(buf[i], k) for k in OBS_FIELDS} for i in range(min(n.value, cap))]
+        rc = kd_step(self._h, dt, nsteps, obs_every, buf if cap > 0 else None, cap, C.byref(n))
+        obs = [{k: getattr(buf[i], k) for k in OBS_FIELDS} for i in range(min(n.value, cap))]
+        if rc == KD_ERR_CANCELLED:
+            raise KdCancelled(rc, kd_last_error().decode(errors="replace"), obs)
+        _check(rc)
+        return obs
+
+    def cancel(self):
+        """Asks the running (or next) ``step`` to stop at its next chunk boundary
+        (``kd_cancel``; callable from another thread)."""
+        _check(kd_cancel(self._h))
 
     def observe(self, spec: W.ObsSpec | None = None) -> dict:
         o = kd_obs()

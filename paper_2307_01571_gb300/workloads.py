@@ -174,6 +174,19 @@ def c3(units: Units = ATOMIC, precision: int = FP32, nsteps: int = 2000) -> Work
                     dt, nsteps, obs_every=100, precision=precision)
 
 
+def hbm(units: Units = ATOMIC, precision: int = FP32, nsteps: int = 200) -> Workload:
+    """A grid whose state does not fit in L2 (4096x2048: 256 MiB spinor in FP32), over a
+    160 lambda x 80 lambda co-moving box, epsilon = 0.02, otherwise as the 1024x512 case."""
+    k, lam = laser(units)
+    dt = dt_of(units)
+    g = Grid(4096, 2048, -80 * lam, 80 * lam, -40 * lam, 40 * lam)
+    f = Field(kind=GAUSS, longitudinal=1, a0=0.1, k_L=k, epsilon=0.02, env_T=0.0,
+              p_shift_x=0.0, p_shift_y=units.mc, box_vy=units.c / math.sqrt(2.0))
+    p = Packet(-units.hbar * k, units.mc, 0.0, 0.0, units.hbar * k / 20.0, 1, 0)
+    return Workload(f"Gaussian-beam standing wave 4096x2048, {nsteps} steps", units, g, f, p,
+                    dt, nsteps, obs_every=100, precision=precision)
+
+
 def small(nx: int, ny: int, kind: int = GAUSS, units: Units = NATURAL, nsteps: int = 20,
           longitudinal: int = 1, a0: float = 0.1, box_vy: float | None = None,
           precision: int = FP64, env: bool = False) -> Workload:

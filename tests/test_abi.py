@@ -85,3 +85,9 @@ def test_launch_variant_count_agrees_everywhere(kd):
     assert _build.SWEEP_VARIANTS == n
     assert kd.KD_SWEEP_VARIANTS == n
     assert sum(1 for u in _build.UNITS if u[0] == "kd_sweep_f32.cu") == n
+
+
+def test_cancel_and_alloc_hook_argument_checks(kd):
+    assert kd.kd_cancel(None) == kd.KD_ERR_ARG
+    assert kd.kd_inject_alloc_failure(-2) == kd.KD_ERR_ARG
+    assert kd.kd_inject_alloc_failure(-1) == kd.KD_OK

@@ -93,6 +93,33 @@ def test_step_random_spinor(kd, prec, fname, nx, ny):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("fname", ["plane", "gauss", "gauss_transverse_static"])
+@pytest.mark.parametrize("nx,ny", [(32, 16), (128, 64)])
+def test_step_large_rotation_angle(kd, prec, fname, nx, ny):
+    """Potential factors with rotation angle theta = tau m c^2 |a| / hbar up to 1: natural
+    units, dt = 0.5 hbar/mc^2 and a0 = 2, so the kernels' closed-form branch for
+    theta >= 1/4 (sin and cos of theta / 2) runs next to the small-angle series."""
+    wl = W.small(nx, ny, units=W.NATURAL, a0=2.0, nsteps=5, **FIELDS[fname])
+    dt = 10 * wl.dt
+    u, g, f = wl.units, wl.grid, wl.field
+    # the largest angle the merged potential factors reach on this grid at the 5 steps
+    theta = 0.0
+    for n in range(1, 5):
+        for x in np.linspace(g.x_min, g.x_max, 33):
+            for y in np.linspace(g.y_min, g.y_max, 9):
+                ax, ay = oracle.field_a(u, f, x, y + f.box_vy * n * dt, n * dt)
+                theta = max(theta, dt * u.mc2 * math.hypot(ax, ay) / u.hbar)
+    assert theta > 0.9
+    psi = W.random_spinor(nx, ny, 11 * nx + ny)
+    ref = oracle.step(u, g, f, psi, 0.0, dt, wl.nsteps)
+    with kd.Sim(u, g, f, prec) as sim:
+        sim.set_spinor(psi)
+        sim.step(dt, wl.nsteps)
+        got = sim.get_spinor()
+    assert rel(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("units", ["atomic", "natural"])
 def test_packet_run_with_observables(kd, prec, units):
     u = W.ATOMIC if units == "atomic" else W.NATURAL
@@ -115,8 +142,6 @@ def test_packet_run_with_observables(kd, prec, units):
     assert len(obs) == 3
     for o, r in zip(obs, refs):
         assert abs(o["t"] - r["t"]) <= 1e-15 * r["t"]
-        for k in W.ObsSpec.__dataclass_fields__:
-            pass
         for k, v in r.items():
             if k == "t":
                 continue

@@ -49,6 +49,22 @@ def test_tc_step_against_oracle(kd, fname, nx, ny):
     assert rel(got, ref) <= 1e-4
 
 
+@pytest.mark.parametrize("fname", ["plane", "gauss"])
+@pytest.mark.parametrize("nx,ny", [(1024, 16), (16, 1024)])
+def test_tc_step_large_rotation_angle(kd, fname, nx, ny):
+    """The tensor-core sweeps' potential step at rotation angles up to ~1 (natural units,
+    dt = 0.5 hbar/mc^2, a0 = 2): the closed-form branch for theta >= 1/4."""
+    wl = W.small(nx, ny, units=W.NATURAL, a0=2.0, nsteps=4, **FIELDS[fname])
+    dt = 10 * wl.dt
+    psi = W.random_spinor(nx, ny, 3 * nx + ny)
+    ref = oracle.step(wl.units, wl.grid, wl.field, psi, 0.0, dt, wl.nsteps)
+    with kd.Sim(wl.units, wl.grid, wl.field, TC) as sim:
+        sim.set_spinor(psi)
+        sim.step(dt, wl.nsteps)
+        got = sim.get_spinor()
+    assert rel(got, ref) <= 1e-4
+
+
 @pytest.mark.parametrize("wlf", [lambda: W.c2(precision=TC, nsteps=3), lambda: W.c3(precision=TC, nsteps=3)])
 def test_tc_full_size_with_observables(kd, wlf):
     wl = wlf()
@@ -132,3 +148,27 @@ def test_tc_member_in_a_batch_matches_it_alone(kd):
     for s, a in zip(sims, alone):
         assert np.array_equal(s.get_spinor(), a)
         s.close()
+
+
+def test_tc_injected_wait_fault_lasts_one_batch_step(kd):
+    """The bounded-wait test hook on a batch member: the next kd_batch_step returns
+    KD_ERR_TIMEOUT (the member's waits give up), the one after it runs normally and
+    matches the member run alone."""
+    wl = W.small(1024, 16, W.GAUSS, units=W.ATOMIC, a0=0.3, nsteps=2)
+    psi = W.random_spinor(1024, 16, 21)
+    with kd.Sim.from_workload(wl.with_(precision=TC)) as alone:
+        alone.set_spinor(psi)
+        alone.step(wl.dt, 2)
+        ref = alone.get_spinor()
+    sim = kd.Sim.from_workload(wl.with_(precision=TC))
+    sim.set_spinor(psi)
+    with kd.Batch([sim]) as b:
+        sim.inject_fault()
+        with pytest.raises(kd.KdError) as e:
+            b.step([wl.dt], 2)
+        assert e.value.code == kd.KD_ERR_TIMEOUT
+        sim.set_spinor(psi)
+        sim.set_time(0.0)
+        b.step([wl.dt], 2)
+    assert np.array_equal(sim.get_spinor(), ref)
+    sim.close()
