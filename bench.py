@@ -34,8 +34,8 @@ UNIT = "grid-point-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 # algorithmic bytes per grid point per Strang step: two read+write sweeps of the
 # four-component spinor (x sweep and y sweep)
-BYTES_PER_PT_STEP = {"fp32": 2 * 2 * 4 * 8, "fp64": 2 * 2 * 4 * 16}
-BYTES_PER_PT_SWEEP = {"fp32": 2 * 4 * 8, "fp64": 2 * 4 * 16}
+BYTES_PER_PT_STEP = {"fp32": 2 * 2 * 4 * 8, "fp64": 2 * 2 * 4 * 16, "dw": 2 * 2 * 4 * 16}
+BYTES_PER_PT_SWEEP = {"fp32": 2 * 4 * 8, "fp64": 2 * 4 * 16, "dw": 2 * 4 * 16}
 # FP64 FMA peak of one GB300 (the recipe's nominal 1.25 TFLOP/s; an FMA-chain probe
 # measured 1.256): the FP64 sweeps are bound by this pipe, not by HBM
 FP64_PEAK_TFLOPS = 1.25
@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-surrogate", action="store_true")
     p.add_argument("--no-tc", action="store_true", help="skip the tensor-core precision form")
     p.add_argument("--no-hbm", action="store_true", help="skip the HBM-resident 4096x2048 grid")
+    p.add_argument("--no-dw", action="store_true", help="skip the double-word (FP64-accurate) form")
     p.add_argument("--profile-sweep", default=None, metavar="PREC,KIND,REPS[,GRID]",
                    help="profiling mode: build the GRID workload (1024x512 default, or 4096x2048), "
                         "step it twice, then run REPS back-to-back sweeps of KIND (0 x, 1 y) at "
@@ -251,6 +252,20 @@ def batched_form(kd, stream, K, barrier, dist):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / K
+    # the persistent form: one kernel per chunk with a device work queue (fixed variants)
+    for s_, w in zip(sims, members):
+        s_.init_packet(w.packet)
+    with kd.Batch(sims, stream=stream.cuda_stream) as b:
+        b.set_mode(kd.KD_BATCH_PERSISTENT)
+        b.step(dts, members[0].nsteps, obs_every=100)           # warm-up: graphs captured
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            b.step(dts, members[0].nsteps, obs_every=100)
+        e1.record(stream)
+        e1.synchronize()
+        ms_p = e0.elapsed_time(e1) / K
     for s_, w in zip(sims, members):                           # the same runs one by one,
         s_.autotune(w.dt)                                      # on the variants tuned alone
         s_.step(w.dt, w.nsteps, obs_every=100)
@@ -269,7 +284,11 @@ def batched_form(kd, stream, K, barrier, dist):
                 "workload": "64 seeded Gaussian-beam runs, grids 128x128..512x256, c64, "
                             "2000 steps, observations every 100",
                 "sequential_value": pts / (ms_seq * 1e-3),
-                "speedup_vs_sequential": ms_seq / ms})
+                "speedup_vs_sequential": ms_seq / ms,
+                "persistent": {"value": pts / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p,
+                               "form": "one persistent kernel per 100-step chunk, device work queue of "
+                                       "(step, sweep, member, block group) items, bounded waits",
+                               "over_graph_branches": ms / ms_p}})
     return res
 
 
@@ -469,7 +488,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def tuned(sim, dt):
-        if args.sweep_variants and sim.precision != W.FP64:
+        if args.sweep_variants and sim.precision in (W.FP32, W.FP32_TC):
             v = tuple(int(x) for x in args.sweep_variants.split(","))
             sim.sweep_variants = v
             return {"variants": v, "ms": {"x": [], "y": []}, "pinned": True}
@@ -597,6 +616,16 @@ def main():
                         "norm_drift": drift64, "speedup_fp32_over_fp64": value / v64,
                         "roofline": roofline_alu(wl64, sw64),
                         "roofline_hbm": roofline("fp64", wl64, sw64, hbm), "gpu_launches": l64}
+    if not args.no_dw:
+        Kd = max(1, min(K, 3))
+        wld, msd, ld, _, driftd, swd, _ = timed_form(W.DW, Kd, 3, False)
+        vd = wld.points * wld.nsteps * Kd * world / (msd * 1e-3)
+        line["dw"] = {"value": vd, "unit": UNIT, "ms_per_step": msd / Kd, "steps": Kd,
+                      "dtype": "f32 pairs (double-word, 48-bit significand)",
+                      "norm_drift": driftd, "gpu_launches": ld,
+                      "roofline_hbm": roofline("dw", wld, swd, hbm)}
+        if "fp64" in line:
+            line["dw"]["speedup_over_fp64"] = vd / line["fp64"]["value"]
     if rank == 0 and not args.no_tc:
         line["precision_form"] = precision_form(kd, stream, not args.no_cpu)
         if "fp64" in line:
@@ -618,8 +647,8 @@ def main():
         wlc = W.c2(precision=W.FP64, nsteps=4)
         r, dt, ref = oracle_rate(wlc, 4)
         errs = {}
-        for prec, name in ((W.FP32, "fp32"), (W.FP64, "fp64")):
-            if prec == W.FP64 and args.no_fp64:
+        for prec, name in ((W.FP32, "fp32"), (W.FP64, "fp64"), (W.DW, "dw")):
+            if (prec == W.FP64 and args.no_fp64) or (prec == W.DW and args.no_dw):
                 continue
             s = kd.Sim.from_workload(wlc.with_(precision=prec), stream=stream.cuda_stream)
             s.init_packet(wlc.packet)
@@ -629,7 +658,7 @@ def main():
             errs[name] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
         line["error_vs_oracle"] = {**errs, "strang_steps": 4, "measure": "max|psi-psi_oracle|/max|psi_oracle|"}
         forms = [(W.FP32, "fp32")] + ([] if args.no_fp64 else [(W.FP64, "fp64")]) + \
-                ([] if args.no_tc else [(W.FP32_TC, "fp32_tc")])
+                ([] if args.no_dw else [(W.DW, "dw")]) + ([] if args.no_tc else [(W.FP32_TC, "fp32_tc")])
         fr = full_run_errors(kd, stream, forms)
         if fr:
             line["error_vs_oracle"]["full_run"] = fr

@@ -11,8 +11,8 @@
  *    kd_last_error() returns a thread-local message describing the last failure.
  *  - A spinor is an array of complex numbers laid out [ny][nx][4], point-major,
  *    components in the Dirac (standard) representation (psi1..psi4), complex128
- *    (interleaved doubles) for KD_FP64 simulations and complex64 for KD_FP32 and
- *    KD_FP32_TC.
+ *    (interleaved doubles) for KD_FP64 and KD_DW simulations and complex64 for KD_FP32
+ *    and KD_FP32_TC.
  *    Row iy, column ix is the point (x_min + ix dx, y_min + iy dy) of the box at t = 0.
  *  - `where` = KD_HOST for a host pointer (the call copies synchronously) or
  *    KD_DEVICE for a device pointer on the simulation's GPU (the call is ordered on the
@@ -56,6 +56,15 @@ extern "C" {
  * sweeps at run ends and axes of other lengths run the KD_FP32 kernels.  State and
  * checkpoints are those of KD_FP32 (interchangeable). */
 #define KD_FP32_TC 2
+/* Double-word form, FP64-accurate on the FP32 pipe: every real of the spinor, the phase
+ * tables and the arithmetic of the step is an unevaluated sum of two floats (48
+ * significand bits; error-free transformations of Knuth, Dekker and Joldes-Muller-Popescu),
+ * the field's exp and sin/cos evaluated to ~1e-14; the FP64 pipe of GB300 runs at 1/64 of
+ * the FP32 pipe.  The step is the same Strang step as KD_FP64 (Sec. II.D); results agree
+ * with FP64 to ~1e-11 relative over thousands of steps.  The ABI's spinors are complex128
+ * as for KD_FP64; read-outs (observables, densities) are computed in FP64 from an FP64
+ * copy of the state.  Device memory as KD_FP64 plus one spinor-sized buffer. */
+#define KD_DW 3
 
 #define KD_HOST 0
 #define KD_DEVICE 1
@@ -123,8 +132,8 @@ typedef struct {
 
 typedef struct kd_sim kd_sim;
 
-/* Creates a simulation on the current CUDA device.  precision is KD_FP64, KD_FP32 or
- * KD_FP32_TC.
+/* Creates a simulation on the current CUDA device.  precision is KD_FP64, KD_FP32,
+ * KD_FP32_TC or KD_DW.
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream) on which every
  * device operation of this simulation is ordered.  The spinor starts at zero, t = 0.
  * Errors: KD_ERR_ARG, KD_ERR_UNSUPPORTED_SIZE, KD_ERR_CUDA, KD_ERR_NOMEM. */
@@ -220,6 +229,22 @@ void kd_batch_destroy(kd_batch* batch);
  * KD_ERR_ARG while the batch's or a member's stream is being captured. */
 int kd_batch_autotune(kd_batch* batch, const double* dt, int32_t steps, int32_t* variants);
 
+/* Persistent form of the batch (KD_BATCH_PERSISTENT): each chunk of steps of all members
+ * runs as ONE kernel launch whose CTAs pull work items (step, sweep, member, group of
+ * blocks) from a device queue in a fixed order; an item waits for its member's previous
+ * sweep through per-member completion counters, each wait bounded by a clock64 budget
+ * (about a second), after which the launch is abandoned and kd_batch_step returns
+ * KD_ERR_TIMEOUT (the members' states are then not valid evolutions).  The observation and
+ * opening-half work at chunk ends runs as graph branches beside it, and the whole chunk is
+ * one CUDA-graph launch.  Every member must be KD_FP32 with both axes of 16 ... 512 points
+ * (else KD_ERR_UNSUPPORTED_SIZE); the members' sweeps run launch variants (x 0, y 3), and a
+ * member advanced this way equals the member advanced alone on those variants, bit for
+ * bit.  KD_BATCH_GRAPH (the default) restores the graph-branch form.  The persistent form
+ * holds device buffers of its own (descriptors and counters, O(n)).  Synchronises. */
+#define KD_BATCH_GRAPH 0
+#define KD_BATCH_PERSISTENT 1
+int kd_batch_set_mode(kd_batch* batch, int32_t mode);
+
 /* Surrogate network (a learned stand-in for the solver's read-outs; the paper has no network): a fully
  * connected MLP, widths[0] inputs -> ... -> widths[nlayers] outputs, exact-erf GELU on the
  * hidden layers, linear output, trained with mean squared error and Adam
@@ -285,9 +310,15 @@ int kd_get_sweep_variants(kd_sim* sim, int32_t* variant_x, int32_t* variant_y);
  * for them gives up after its iteration limit (about a second); the kernels then skip
  * their remaining work, free their tensor memory and set the simulation's status, and
  * kd_step returns KD_ERR_TIMEOUT with the context intact; the state is then not a valid
- * evolution (restore a checkpoint or set a new spinor).  kind 0 cancels.  KD_ERR_ARG for other kinds or when the
- * simulation is not KD_FP32_TC. */
+ * evolution (restore a checkpoint or set a new spinor).  kind 0 cancels either hook.
+ * KD_ERR_ARG for other kinds, or for KD_FAULT_TC_WAIT when the simulation is not
+ * KD_FP32_TC. */
 #define KD_FAULT_TC_WAIT 1
+/* kind KD_FAULT_PERSIST_HOLD: in the next kd_batch_step of a persistent batch holding the
+ * simulation, the completion of the simulation's first work item is never signalled, so
+ * the items that depend on it wait until their bounded waits give up and the call returns
+ * KD_ERR_TIMEOUT (no fault, trap or hang); any precision. */
+#define KD_FAULT_PERSIST_HOLD 2
 int kd_inject_fault(kd_sim* sim, int32_t kind);
 
 /* Requests that the kd_step running on this simulation (in another host thread), or the

@@ -1,7 +1,7 @@
 """Compiles the CUDA library ``libkd.so`` in-tree for sm_103a.
 
-The translation units (host API, the FP32 sweeps once per launch variant, the FP64
-sweeps, the tensor-core sweeps, the allocation-free entry and the MLP kernels) compile in parallel with nvcc; the
+The translation units (host API, the FP32 sweeps once per launch variant, the
+double-word sweeps once per axis and shape, the FP64 sweeps, the tensor-core sweeps, the allocation-free entry and the MLP kernels) compile in parallel with nvcc; the
 CUDA runtime is linked statically so the library only needs the driver.
 """
 from __future__ import annotations
@@ -21,8 +21,10 @@ SWEEP_VARIANTS = 4    # KD_SWEEP_VARIANTS in csrc/kd_internal.h
 UNITS = ([("kd_api.cu", "kd_api.o", [])]
          + [("kd_sweep_f32.cu", f"kd_sweep_f32_v{v}.o", [f"-DKD_SWEEP_VARIANT={v}"])
             for v in range(SWEEP_VARIANTS)]
+         + [("kd_sweep_dw.cu", f"kd_sweep_dw_p{p}.o", [f"-DKD_DW_PART={p}"]) for p in range(6)]
          + [("kd_sweep_f64.cu", "kd_sweep_f64.o", []), ("kd_tc.cu", "kd_tc.o", []),
-            ("kd_noalloc.cu", "kd_noalloc.o", []), ("kd_mlp.cu", "kd_mlp.o", [])])
+            ("kd_noalloc.cu", "kd_noalloc.o", []), ("kd_mlp.cu", "kd_mlp.o", []),
+            ("kd_persist.cu", "kd_persist.o", [])])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{os.path.join(ROOT, 'include')}"]

@@ -22,7 +22,9 @@
 #include <vector>
 
 #include "../../include/kd.h"
+#include "kd_dw.cuh"
 #include "kd_internal.h"
+#include "kd_persist.h"
 
 using namespace kd;
 
@@ -133,6 +135,14 @@ struct kd_sim {
     void* tc_tw = nullptr;
     float* tc_scale = nullptr;
     int tc_fault = 0;          // kd_inject_fault: applies to the next kd_step call only
+    int persist_hold = 0;      // kd_inject_fault(KD_FAULT_PERSIST_HOLD): next persistent batch step
+    // double-word form (KD_DW): the state psi and the tables xtab, kxtab, kytab, ktab hold
+    // float pairs; prec stays KD_FP64 for the observation path, which reads an FP64 copy
+    // of the state (view) and runs the FP64 transforms on it
+    bool dw = false;
+    void* tw_dw[2] = {};       // double-word twiddles per axis
+    void* dwconst = nullptr;   // DWConst (exp and sin/cos tables)
+    void* view = nullptr;      // FP64 copy of the state for read-outs
     std::atomic<int> cancel{0};  // kd_cancel: the running or next kd_step stops early
     // kd_step keeps at most kRunAhead chunks in flight (host waits on the event of the
     // chunk kRunAhead back), so that a cancellation stops work that is not yet queued
@@ -554,6 +564,25 @@ __global__ void k_obs_reduce(const double* rowsum, const double* cells, int nx, 
     }
 }
 
+// Double-word form: n doubles -> n float pairs (h, l) in the same 8-byte slots (in place
+// allowed), and back.
+__global__ void k_dw_from_f64(void* buf, size_t n) {
+    double* d = (double*)buf;
+    float2* f = (float2*)buf;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const DW w = dw_from_double(d[i]);
+        f[i] = make_float2(w.h, w.l);
+    }
+}
+__global__ void k_dw_to_f64(const void* in, void* out, size_t n) {
+    const float2* f = (const float2*)in;
+    double* d = (double*)out;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 w = f[i];
+        d[i] = dw_to_double(DW{w.x, w.y});
+    }
+}
+
 // Layout conversion between the ABI's [P][4] Dirac order and the internal pair planes.
 template <typename T>
 __global__ void k_permute(const T* in, T* out, size_t npts, int to_internal) {
@@ -571,6 +600,66 @@ __global__ void k_permute(const T* in, T* out, size_t npts, int to_internal) {
 // ---------------------------------------------------------------- host helpers ----
 
 int grid_blocks(size_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+int dw_from_f64_launch(kd_sim* s, void* buf, size_t n) {
+    const int b = grid_blocks(n, 256) < 4096 ? grid_blocks(n, 256) : 4096;
+    k_dw_from_f64<<<b, 256, 0, s->stream>>>(buf, n);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    return KD_OK;
+}
+
+// The state as FP64 (the internal pair-plane layout): psi itself, or for the double-word
+// form an FP64 copy in s->view.
+int state_view(kd_sim* s, const void** out) {
+    if (!s->dw) { *out = s->psi; return KD_OK; }
+    const size_t n = s->P * 8;
+    const int b = grid_blocks(n, 256) < 4096 ? grid_blocks(n, 256) : 4096;
+    k_dw_to_f64<<<b, 256, 0, s->stream>>>(s->psi, s->view, n);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    *out = s->view;
+    return KD_OK;
+}
+
+// Double-word form: the per-x field table as float4 [2][nx][2] (each FP64 4-vector as two
+// pairs of double-words), pi_x as float2, the twiddle tables of the double-word launch
+// shapes, and the exp / sin-cos constant tables, from the FP64 values.
+template <typename T> int upload_dw_tables(kd_sim* s, const std::vector<T>& xt, const std::vector<T>& kx) {
+    const int nx = s->g.nx;
+    std::vector<float4> xd(4 * (size_t)nx);
+    for (size_t i = 0; i < 2 * (size_t)nx; ++i) {
+        const DW a = dw_from_double((double)xt[4 * i]), b = dw_from_double((double)xt[4 * i + 1]);
+        const DW c = dw_from_double((double)xt[4 * i + 2]), d = dw_from_double((double)xt[4 * i + 3]);
+        xd[2 * i] = make_float4(a.h, a.l, b.h, b.l);
+        xd[2 * i + 1] = make_float4(c.h, c.l, d.h, d.l);
+    }
+    KD_CUDA(cudaMemcpy(s->xtab, xd.data(), xd.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    std::vector<float2> kd2(nx);
+    for (int i = 0; i < nx; ++i) {
+        const DW a = dw_from_double((double)kx[i]);
+        kd2[i] = make_float2(a.h, a.l);
+    }
+    KD_CUDA(cudaMemcpy(s->kxtab, kd2.data(), kd2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    for (int ax = 0; ax < 2; ++ax) {
+        const int logn = ax == 0 ? s->lx : s->ly;
+        int entries = 0;
+        KD_CUDA(build_twiddles_dw(logn, sweep_loge_dw(logn), s->tw_dw[ax], &entries, s->stream));
+        if (entries > 2 * (1 << logn)) return fail(KD_ERR_CUDA, "twiddle table overflow");
+    }
+    DWConst K;
+    for (int j = -13; j <= 13; ++j) {
+        const DW sn = dw_from_double(sin(j / 16.0)), cs = dw_from_double(cos(j / 16.0));
+        K.sc[j + 13] = make_float4(sn.h, sn.l, cs.h, cs.l);
+    }
+    for (int j = 0; j < 32; ++j) {
+        const DW e = dw_from_double(exp2(-j / 32.0));
+        K.e2[j] = make_float2(e.h, e.l);
+    }
+    KD_CUDA(cudaMemcpy(s->dwconst, &K, sizeof K, cudaMemcpyHostToDevice));
+    KD_CUDA(cudaStreamSynchronize(s->stream));
+    return KD_OK;
+}
 
 template <typename T> int upload_tables_t(kd_sim* s) {
     const int nx = s->g.nx;
@@ -610,11 +699,12 @@ template <typename T> int upload_tables_t(kd_sim* s) {
             e1[2] = (T)sin(zeta);
         }
     }
-    KD_CUDA(cudaMemcpy(s->xtab, xt.data(), xt.size() * sizeof(T), cudaMemcpyHostToDevice));
     // kinetic x momentum per column
     std::vector<T> kx(nx);
     const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
     for (int i = 0; i < nx; ++i) kx[i] = (T)(dpx * signed_index(i, nx) + s->f.p_shift_x);
+    if (s->dw) return upload_dw_tables(s, xt, kx);
+    KD_CUDA(cudaMemcpy(s->xtab, xt.data(), xt.size() * sizeof(T), cudaMemcpyHostToDevice));
     KD_CUDA(cudaMemcpy(s->kxtab, kx.data(), kx.size() * sizeof(T), cudaMemcpyHostToDevice));
     return KD_OK;
 }
@@ -747,13 +837,30 @@ template <typename T> int build_dt_tables_t(kd_sim* s, double dt) {
         unit_phase<T>(s->f.box_vy * py * dt / s->u.hbar, &ky[4 * j + 1], &ky[4 * j + 2]);
         ky[4 * j + 3] = (T)0;
     }
-    KD_CUDA(cudaMemcpyAsync(s->kytab, ky.data(), ky.size() * sizeof(T), cudaMemcpyHostToDevice,
-                            s->stream));
+    std::vector<float4> kyd;
+    if (s->dw) {   // per row (pi_y | cos phi - 1) and (sin phi | 0) as double-words
+        kyd.resize(2 * (size_t)ny);
+        for (int j = 0; j < ny; ++j) {
+            const DW a = dw_from_double((double)ky[4 * j]), b = dw_from_double((double)ky[4 * j + 1]);
+            const DW c = dw_from_double((double)ky[4 * j + 2]);
+            kyd[2 * j] = make_float4(a.h, a.l, b.h, b.l);
+            kyd[2 * j + 1] = make_float4(c.h, c.l, 0.0f, 0.0f);
+        }
+        KD_CUDA(cudaMemcpyAsync(s->kytab, kyd.data(), kyd.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                                s->stream));
+    } else {
+        KD_CUDA(cudaMemcpyAsync(s->kytab, ky.data(), ky.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                s->stream));
+    }
     k_ktab<T><<<grid_blocks(s->P, 256), 256, 0, s->stream>>>(
         (T*)s->ktab, nx, ny, dpx, dpy, s->f.p_shift_x, s->f.p_shift_y, s->u.c, mc2, s->u.hbar, dt,
         (const T*)s->kxtab, (const T*)s->kytab, s->u.m * s->u.c);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
+    if (s->dw) {   // (C - 1)/P and c S/P as double-words, in place
+        int rc = dw_from_f64_launch(s, s->ktab, 2 * s->P);
+        if (rc) return rc;
+    }
     KD_CUDA(cudaStreamSynchronize(s->stream));
     s->ktab_dt = dt;
     return KD_OK;
@@ -763,8 +870,10 @@ int build_dt_tables(kd_sim* s, double dt) {
     return s->prec == KD_FP64 ? build_dt_tables_t<double>(s, dt) : build_dt_tables_t<float>(s, dt);
 }
 
-cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* out, int n_local,
-                  double tau) {
+// One fused sweep of the state (the simulation's own form), or, with view = true, an FP64
+// transform of the FP64 view of the state (read-outs of the double-word form).
+SweepArgs make_args(const kd_sim* s, int axis, int op, const void* in, void* out, int n_local,
+                    double tau, bool view) {
     SweepArgs a{};
     a.in = in;
     a.out = out;
@@ -773,7 +882,9 @@ cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* 
     a.op = op;
     const int logn = axis == AXIS_X ? s->lx : s->ly;
     const int var = s->prec == KD_FP64 ? 0 : s->var[axis];
-    a.tw = s->tw[axis][sweep_loge(s->prec == KD_FP64, axis, logn, var) - 2];
+    const bool dwk = s->dw && !view;   // the double-word kernels
+    a.tw = dwk ? s->tw_dw[axis] : s->tw[axis][sweep_loge(s->prec == KD_FP64, axis, logn, var) - 2];
+    a.dwconst = s->dwconst;
     a.clock = s->clock;
     a.steps = s->steps;
     a.n_local = n_local;
@@ -799,8 +910,18 @@ cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* 
     a.tc_scale = s->tc_scale;
     a.status = s->status;
     a.tc_fault = s->tc_fault;
+    return a;
+}
+
+cudaError_t sweep(kd_sim* s, int axis, int shape, int op, const void* in, void* out, int n_local,
+                  double tau, bool view = false) {
+    const SweepArgs a = make_args(s, axis, op, in, out, n_local, tau, view);
+    const int logn = axis == AXIS_X ? s->lx : s->ly;
+    const int var = s->prec == KD_FP64 ? 0 : s->var[axis];
+    const bool dwk = s->dw && !view;
     ++s->launches;
     if (s->tc && shape == SHAPE_F1F2 && tc_supported(logn)) return launch_tc_sweep(axis, a, s->stream);
+    if (dwk) return launch_sweep_dw(axis, shape, logn, a, s->stream);
     return s->prec == KD_FP64 ? launch_sweep_f64(axis, shape, logn, a, s->stream)
                               : launch_sweep_f32(var, axis, shape, logn, a, s->stream);
 }
@@ -902,7 +1023,7 @@ int time_sweep(kd_sim* s, int axis, int reps, double dt, float* ms) {
             return fail(KD_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));          \
     } while (0)
 
-int rowsum_launch(kd_sim* s, const void* psi) {
+int rowsum_launch(kd_sim* s, const void* psi) {   // psi: FP64 for KD_FP64 and KD_DW (view)
     if (s->prec == KD_FP64) k_rowsum<double><<<s->g.ny, 256, 0, s->stream>>>((const double*)psi, s->g.nx, s->g.ny, s->rowsum);
     else k_rowsum<float><<<s->g.ny, 256, 0, s->stream>>>((const float*)psi, s->g.nx, s->g.ny, s->rowsum);
     KD_CUDA(cudaGetLastError());
@@ -920,8 +1041,11 @@ int momentum_density_launch(kd_sim* s, int basis, double* out) {
     const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
     const double dpy = s->u.hbar * 2.0 * kPi / (s->g.y_max - s->g.y_min);
     const double mc2 = s->u.m * s->u.c * s->u.c;
-    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_NONE, s->psi, s->work, 0, 0.0));
-    KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F1, OP_NONE, s->work, s->work, 0, 0.0));
+    const void* st = nullptr;
+    int rc = state_view(s, &st);
+    if (rc) return rc;
+    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_NONE, st, s->work, 0, 0.0, true));
+    KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F1, OP_NONE, s->work, s->work, 0, 0.0, true));
     const double cellw = dxdy(s) / (double)s->P;
     if (s->prec == KD_FP64)
         k_momentum_density<double><<<grid_blocks(s->P, 256), 256, 0, s->stream>>>(
@@ -975,10 +1099,13 @@ int observe_launch(kd_sim* s, const ObsWin& w, int basis, bool in_step, int n_lo
                    int64_t obs_every, int64_t cap, kd_obs* out) {
     int rc = ensure_md(s);
     if (rc) return rc;
-    rc = rowsum_launch(s, s->psi);
+    const void* st = nullptr;
+    rc = state_view(s, &st);
     if (rc) return rc;
-    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_NONE, s->psi, s->work, 0, 0.0));
-    KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F1, OP_NONE, s->work, s->work, 0, 0.0));
+    rc = rowsum_launch(s, st);
+    if (rc) return rc;
+    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_NONE, st, s->work, 0, 0.0, true));
+    KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F1, OP_NONE, s->work, s->work, 0, 0.0, true));
     {
         const double dpx = s->u.hbar * 2.0 * kPi / (s->g.x_max - s->g.x_min);
         const double dpy = s->u.hbar * 2.0 * kPi / (s->g.y_max - s->g.y_min);
@@ -1102,6 +1229,7 @@ uint64_t param_hash(const kd_sim* s) {
     h = fnv(h, &s->g, sizeof s->g);
     h = fnv(h, &s->f, sizeof s->f);
     h = fnv(h, &s->prec, sizeof s->prec);
+    if (s->dw) h = fnv(h, &s->dw, sizeof s->dw);
     return h;
 }
 
@@ -1133,6 +1261,10 @@ int copy_in(kd_sim* s, const void* psi, int32_t where) {
     else k_permute<float><<<blocks, 256, 0, s->stream>>>((const float*)src, (float*)s->psi, s->P, 1);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
+    if (s->dw) {
+        int rc = dw_from_f64_launch(s, s->psi, s->P * 8);
+        if (rc) return rc;
+    }
     if (where == KD_HOST) KD_CUDA(cudaStreamSynchronize(s->stream));
     return KD_OK;
 }
@@ -1141,8 +1273,11 @@ int copy_out(kd_sim* s, void* psi, int32_t where) {
     const size_t bytes = spinor_bytes(s);
     void* dst = where == KD_HOST ? s->work : psi;
     const int blocks = grid_blocks(s->P, 256) < 4096 ? grid_blocks(s->P, 256) : 4096;
-    if (s->prec == KD_FP64) k_permute<double><<<blocks, 256, 0, s->stream>>>((const double*)s->psi, (double*)dst, s->P, 0);
-    else k_permute<float><<<blocks, 256, 0, s->stream>>>((const float*)s->psi, (float*)dst, s->P, 0);
+    const void* st = nullptr;
+    int rc = state_view(s, &st);
+    if (rc) return rc;
+    if (s->prec == KD_FP64) k_permute<double><<<blocks, 256, 0, s->stream>>>((const double*)st, (double*)dst, s->P, 0);
+    else k_permute<float><<<blocks, 256, 0, s->stream>>>((const float*)st, (float*)dst, s->P, 0);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
     if (where == KD_HOST) {
@@ -1167,8 +1302,8 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
     g_err.clear();
     if (!units || !grid || !field || !out) return fail(KD_ERR_ARG, "null argument");
     *out = nullptr;
-    if (precision != KD_FP64 && precision != KD_FP32 && precision != KD_FP32_TC)
-        return fail(KD_ERR_ARG, "precision must be KD_FP64, KD_FP32 or KD_FP32_TC");
+    if (precision != KD_FP64 && precision != KD_FP32 && precision != KD_FP32_TC && precision != KD_DW)
+        return fail(KD_ERR_ARG, "precision must be KD_FP64, KD_FP32, KD_FP32_TC or KD_DW");
     if (!pow2_in_range(grid->nx) || !pow2_in_range(grid->ny))
         return fail(KD_ERR_UNSUPPORTED_SIZE, "nx=%d ny=%d: need powers of two in [4, 4096]", grid->nx, grid->ny);
     if (!(grid->x_max > grid->x_min) || !(grid->y_max > grid->y_min) || !isfinite(grid->x_min) ||
@@ -1197,8 +1332,9 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
     s->g = *grid;
     s->f = *field;
     s->tc = precision == KD_FP32_TC;       // FP32 storage and tables, tensor-core sweeps
-    s->prec = s->tc ? KD_FP32 : precision;
-    s->tsize = precision == KD_FP64 ? 8 : 4;
+    s->dw = precision == KD_DW;            // float-pair storage and tables, FP64 read-outs
+    s->prec = s->tc ? KD_FP32 : (s->dw ? KD_FP64 : precision);
+    s->tsize = s->prec == KD_FP64 ? 8 : 4;
     s->stream = (cudaStream_t)cuda_stream;
     s->device = dev;
     s->lx = ilog2(grid->nx);
@@ -1230,6 +1366,12 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
     KD_ALLOC(s->rowsum, (size_t)grid->ny * sizeof(double));
     KD_ALLOC(s->scalar, 4 * sizeof(double));
     KD_ALLOC(s->status, sizeof(int));
+    if (s->dw) {
+        KD_ALLOC(s->tw_dw[AXIS_X], 2 * (size_t)grid->nx * 16);
+        KD_ALLOC(s->tw_dw[AXIS_Y], 2 * (size_t)grid->ny * 16);
+        KD_ALLOC(s->dwconst, sizeof(DWConst));
+        KD_ALLOC(s->view, spinor_bytes(s));
+    }
     if (s->tc) {
         KD_ALLOC(s->tc_b, kTcBImageBytes);
         KD_ALLOC(s->tc_tw, 1024 * sizeof(float2));
@@ -1241,7 +1383,7 @@ int kd_create(const kd_units* units, const kd_grid* grid, const kd_field* field,
         cudaMemset(s->scalar, 0, 4 * sizeof(double)) != cudaSuccess ||
         cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess)
         return bail(fail(KD_ERR_CUDA, "memset failed"));
-    int rc = precision == KD_FP64 ? upload_tables_t<double>(s) : upload_tables_t<float>(s);
+    int rc = s->prec == KD_FP64 ? upload_tables_t<double>(s) : upload_tables_t<float>(s);
     if (rc) return bail(rc);
     if (s->tc) {
         rc = upload_tc_tables(s);
@@ -1260,7 +1402,8 @@ void kd_destroy(kd_sim* s) {
     clear_graphs(s);
     void* bufs[] = {s->psi, s->work, s->tw[0][0], s->tw[0][1], s->tw[1][0], s->tw[1][1], s->xtab,
                     s->kxtab, s->kytab, s->ktab, s->clock, s->steps, s->rowsum, s->md, s->scalar,
-                    s->obs_dev, s->status, s->tc_b, s->tc_tw, s->tc_scale};
+                    s->obs_dev, s->status, s->tc_b, s->tc_tw, s->tc_scale, s->tw_dw[0], s->tw_dw[1],
+                    s->dwconst, s->view};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -1345,8 +1488,9 @@ int kd_init_packet(kd_sim* s, const kd_packet* pk) {
             pk->p0y, rx, ry, pk->sigma_p, pk->spin, pk->basis, s->u.c, mc2, s->u.hbar);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
-    KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F2, OP_NONE, s->psi, s->psi, 0, 0.0));
-    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F1, OP_NONE, s->psi, s->psi, 0, 0.0));
+    // the packet is built in FP64 in place (also for the double-word form, converted below)
+    KD_LAUNCH(sweep(s, AXIS_Y, SHAPE_F2, OP_NONE, s->psi, s->psi, 0, 0.0, true));
+    KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F1, OP_NONE, s->psi, s->psi, 0, 0.0, true));
     rc = rowsum_launch(s, s->psi);
     if (rc) return rc;
     k_norm<<<1, 256, 0, s->stream>>>(s->rowsum, s->g.ny, dxdy(s), s->scalar, 0);
@@ -1357,6 +1501,10 @@ int kd_init_packet(kd_sim* s, const kd_packet* pk) {
     else k_scale_by_norm<float><<<1024, 256, 0, s->stream>>>((float*)s->psi, nreal, s->scalar);
     KD_CUDA(cudaGetLastError());
     ++s->launches;
+    if (s->dw) {
+        rc = dw_from_f64_launch(s, s->psi, nreal);
+        if (rc) return rc;
+    }
     KD_CUDA(cudaStreamSynchronize(s->stream));
     s->t0 = 0.0;
     s->step = 0;
@@ -1460,7 +1608,9 @@ int enqueue_prologue(kd_sim* s, const StepPlan& p) {
     if (p.nobs > 0 || s->tc) {
         KD_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), s->stream));
         if (p.nobs > 0 && s->watch_tol > 0) {
-            int rc = rowsum_launch(s, s->psi);
+            const void* st = nullptr;
+            int rc = state_view(s, &st);
+            if (!rc) rc = rowsum_launch(s, st);
             if (rc) return rc;
             k_norm<<<1, 256, 0, s->stream>>>(s->rowsum, s->g.ny, dxdy(s), s->scalar, 1);
             KD_CUDA(cudaGetLastError());
@@ -1573,9 +1723,11 @@ int kd_step(kd_sim* s, double dt, int64_t nsteps, int64_t obs_every, kd_obs* obs
 int kd_inject_fault(kd_sim* s, int32_t kind) {
     int rc = check_sim(s);
     if (rc) return rc;
-    if (kind != 0 && kind != KD_FAULT_TC_WAIT) return fail(KD_ERR_ARG, "unknown fault kind %d", kind);
+    if (kind != 0 && kind != KD_FAULT_TC_WAIT && kind != KD_FAULT_PERSIST_HOLD)
+        return fail(KD_ERR_ARG, "unknown fault kind %d", kind);
     if (kind == KD_FAULT_TC_WAIT && !s->tc) return fail(KD_ERR_ARG, "not a KD_FP32_TC simulation");
     s->tc_fault = kind == KD_FAULT_TC_WAIT;
+    s->persist_hold = kind == KD_FAULT_PERSIST_HOLD;
     clear_graphs(s);
     return KD_OK;
 }
@@ -1604,9 +1756,89 @@ struct kd_batch {
     // one graph per chunk shape: all simulations' chunks as concurrent branches
     std::map<GraphKey, std::pair<cudaGraphExec_t, std::vector<int64_t>>> graphs;
     std::vector<uint64_t> gens;      // simulations' graph generations the graphs were built on
+    // persistent form (kd_batch_set_mode): member descriptors, prefix sums of the work
+    // items, queue head + per-member completion counters, abort flag
+    bool persistent = false;
+    PersistMember* d_members = nullptr;
+    int* d_pre = nullptr;            // [2 (n + 1)]: y items, x items
+    unsigned* d_ctr = nullptr;       // [1 + n]: queue head, then completion counters
+    int* d_abort = nullptr;
+    int y_items = 0, x_items = 0;
+    int hold_item = -1;              // withheld completion of the current step call (test hook)
 };
 
 namespace {
+
+// Persistent form: uploads this call's member descriptors and the work items' prefix
+// sums, clears the abort flag, and finds the item whose completion the test hook withholds
+// (the first y item of the first held member in the call's first chunk).
+int persist_upload(kd_batch* b, const std::vector<StepPlan>& plans, bool* hold) {
+    const size_t n = b->sims.size();
+    std::vector<PersistMember> hm(n);
+    std::vector<int> pre(2 * (n + 1), 0);
+    b->hold_item = -1;
+    for (size_t i = 0; i < n; ++i) {
+        kd_sim* s = b->sims[i];
+        PersistMember& m = hm[i];
+        m.y = make_args(s, AXIS_Y, OP_KINETIC, s->psi, s->psi, 0, 0.0, false);
+        m.x = make_args(s, AXIS_X, OP_POTENTIAL, s->psi, s->psi, 0, plans[i].dt, false);
+        m.xc = make_args(s, AXIS_X, OP_POTENTIAL, s->psi, s->psi, 0, 0.5 * plans[i].dt, false);
+        m.lx = s->lx;
+        m.ly = s->ly;
+        m.iy = persist_items(AXIS_Y, s->ly, s->g.nx);
+        m.ix = persist_items(AXIS_X, s->lx, s->g.ny);
+        m.status = s->status;
+        pre[i + 1] = pre[i] + m.iy;
+        pre[n + 1 + i + 1] = pre[n + 1 + i] + m.ix;
+        if (s->persist_hold && b->hold_item < 0) b->hold_item = pre[i];
+    }
+    b->y_items = pre[n];
+    b->x_items = pre[2 * n + 1];
+    *hold = b->hold_item >= 0;
+    KD_CUDA(cudaMemcpyAsync(b->d_members, hm.data(), n * sizeof(PersistMember), cudaMemcpyHostToDevice,
+                            b->stream));
+    KD_CUDA(cudaMemcpyAsync(b->d_pre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            b->stream));
+    KD_CUDA(cudaMemsetAsync(b->d_abort, 0, sizeof(int), b->stream));
+    KD_CUDA(cudaStreamSynchronize(b->stream));   // the host vectors go out of scope
+    return KD_OK;
+}
+
+PersistPlan persist_plan(const kd_batch* b, int chunk, bool closing, int hold_item) {
+    const int n = (int)b->sims.size();
+    PersistPlan p{};
+    p.members = b->d_members;
+    p.n = n;
+    p.pre_y = b->d_pre;
+    p.pre_x = b->d_pre + n + 1;
+    p.y_items = b->y_items;
+    p.items_per_step = b->y_items + b->x_items;
+    p.chunk = chunk;
+    p.closing = closing ? 1 : 0;
+    p.next = b->d_ctr;
+    p.done = b->d_ctr + 1;
+    p.abort = b->d_abort;
+    p.budget_cycles = 2000000000LL;   // ~1 s at the GB300's clocks
+    p.hold_item = hold_item;
+    return p;
+}
+
+// A member's work after the persistent launch of a chunk (the launch ran its steps and, on
+// a closing chunk, the closing half sweep): observation, the next opening half sweep, and
+// the device clock, as enqueue_chunk does after its last step.
+int persist_tail(kd_sim* s, const StepPlan& p, int chunk, bool last, bool obs) {
+    if (last || obs) {
+        if (obs) {
+            int rc = observe_launch(s, p.w, s->spec.basis, true, chunk, 0.0, p.obs_every, p.cap, s->obs_dev);
+            if (rc) return rc;
+        }
+        if (!last) KD_LAUNCH(sweep(s, AXIS_X, SHAPE_F2, OP_POTENTIAL, s->psi, s->psi, chunk, 0.5 * p.dt));
+    }
+    k_advance_clock<<<1, 1, 0, s->stream>>>(s->clock, chunk);
+    KD_CUDA(cudaGetLastError());
+    ++s->launches;
+    return KD_OK;
+}
 
 void clear_batch_graphs(kd_batch* b) {
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.first);
@@ -1672,6 +1904,9 @@ void kd_batch_destroy(kd_batch* b) {
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
     clear_batch_graphs(b);
+    void* bufs[] = {b->d_members, b->d_pre, b->d_ctr, b->d_abort};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
     for (cudaEvent_t e : b->join)
         if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -1700,18 +1935,41 @@ int kd_batch_step(kd_batch* b, const double* dt, int64_t nsteps, int64_t obs_eve
         }
     int rc = fork_join(b, b->stream, [&](kd_sim* s, size_t i) { return enqueue_prologue(s, plans[i]); });
     if (rc) return rc;
+    // persistent form: this call's member descriptors (dt, tables, per-step scalars), the
+    // withheld-completion test hook, a cleared abort flag
+    bool hold = false;
+    if (b->persistent) {
+        rc = persist_upload(b, plans, &hold);
+        if (rc) return rc;
+    }
+    bool first_chunk = true;
     rc = for_each_chunk(plans[0], [&](int chunk, bool last, bool obs) -> int {
         GraphKey key{chunk, last ? 1 : 0, obs ? 1 : 0};
+        const bool held = hold && first_chunk;   // this chunk's graph carries the hook
+        first_chunk = false;
+        if (held) clear_batch_graphs(b);
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
             std::vector<int64_t> nodes(n, 0);
             cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return fail(KD_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
-            int crc = fork_join(b, b->cap, [&](kd_sim* s, size_t i) {
+            int crc = KD_OK;
+            if (b->persistent) {
+                // one launch for every member's steps of the chunk, then the members'
+                // observation / opening tails and clocks as branches
+                PersistPlan pl = persist_plan(b, chunk, last || obs, held ? b->hold_item : -1);
+                if (cudaMemsetAsync(b->d_ctr, 0, (1 + n) * sizeof(unsigned), b->cap) != cudaSuccess ||
+                    launch_persist(pl, b->cap) != cudaSuccess)
+                    crc = fail(KD_ERR_CUDA, "persistent batch launch failed");
+                b->sims[0]->launches += 1;
+                nodes[0] += 1;
+            }
+            if (crc == KD_OK) crc = fork_join(b, b->cap, [&](kd_sim* s, size_t i) {
                 const int64_t before = s->launches;
-                int r = enqueue_chunk(s, plans[i].dt, chunk, last, obs, plans[i].w, plans[i].obs_every,
-                                      plans[i].cap);
-                nodes[i] = s->launches - before;
+                int r = b->persistent ? persist_tail(s, plans[i], chunk, last, obs)
+                                      : enqueue_chunk(s, plans[i].dt, chunk, last, obs, plans[i].w,
+                                                      plans[i].obs_every, plans[i].cap);
+                nodes[i] += s->launches - before;
                 s->launches = before;
                 return r;
             });
@@ -1727,15 +1985,25 @@ int kd_batch_step(kd_batch* b, const double* dt, int64_t nsteps, int64_t obs_eve
         }
         KD_CUDA(cudaGraphLaunch(it->second.first, b->stream));
         for (size_t i = 0; i < n; ++i) b->sims[i]->launches += it->second.second[i];
+        if (held) clear_batch_graphs(b);   // the hook lasts one chunk of one call
         return KD_OK;
     });
     if (rc) return rc;
     int first_err = KD_OK;
+    if (b->persistent) {
+        int ab = 0;
+        KD_CUDA(cudaMemcpyAsync(&ab, b->d_abort, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        KD_CUDA(cudaStreamSynchronize(b->stream));
+        for (kd_sim* s : b->sims) s->persist_hold = 0;
+        if (ab) first_err = fail(KD_ERR_TIMEOUT, "persistent batch: a bounded wait for a member's "
+                                                 "previous sweep gave up (states are not valid)");
+    }
     for (size_t i = 0; i < n; ++i) {
         kd_sim* s = b->sims[i];
         cudaStream_t saved = s->stream;
         s->stream = b->stream;   // all branches are joined on the batch stream
         int r = finish_step(s, plans[i], obs_out ? obs_out + i * (size_t)obs_cap : nullptr, n_obs);
+        if (r && first_err == KD_ERR_TIMEOUT) r = KD_OK;   // already reported
         s->stream = saved;
         if (r && !first_err) first_err = r;
         if (s->tc_fault) {   // an injected fault lasts one step call, batched or not
@@ -1744,6 +2012,33 @@ int kd_batch_step(kd_batch* b, const double* dt, int64_t nsteps, int64_t obs_eve
         }
     }
     return first_err;
+}
+
+int kd_batch_set_mode(kd_batch* b, int32_t mode) {
+    if (!b) return fail(KD_ERR_ARG, "null batch");
+    if (mode != KD_BATCH_GRAPH && mode != KD_BATCH_PERSISTENT) return fail(KD_ERR_ARG, "unknown batch mode %d", mode);
+    KD_CUDA(cudaSetDevice(b->device));
+    if (mode == KD_BATCH_PERSISTENT) {
+        for (size_t i = 0; i < b->sims.size(); ++i) {
+            const kd_sim* s = b->sims[i];
+            if (s->prec != KD_FP32 || s->tc || s->dw)
+                return fail(KD_ERR_UNSUPPORTED_SIZE, "persistent batch: member %zu is not a KD_FP32 simulation", i);
+            if (!persist_supported(s->lx) || !persist_supported(s->ly))
+                return fail(KD_ERR_UNSUPPORTED_SIZE, "persistent batch: member %zu grid %dx%d outside 16..512 per axis",
+                            i, s->g.nx, s->g.ny);
+        }
+        const size_t n = b->sims.size();
+        if (!b->d_members) {
+            KD_CUDA(dev_alloc((void**)&b->d_members, n * sizeof(PersistMember)));
+            KD_CUDA(dev_alloc((void**)&b->d_pre, 2 * (n + 1) * sizeof(int)));
+            KD_CUDA(dev_alloc((void**)&b->d_ctr, (1 + n) * sizeof(unsigned)));
+            KD_CUDA(dev_alloc((void**)&b->d_abort, sizeof(int)));
+        }
+    }
+    KD_CUDA(cudaStreamSynchronize(b->stream));
+    b->persistent = mode == KD_BATCH_PERSISTENT;
+    clear_batch_graphs(b);
+    return KD_OK;
 }
 
 int kd_batch_autotune(kd_batch* b, const double* dt, int32_t steps, int32_t* variants) {
@@ -1910,7 +2205,10 @@ int kd_get_density_x(kd_sim* s, double* out, int32_t where) {
         dst = s->md;
     }
     const double dy = (s->g.y_max - s->g.y_min) / s->g.ny;
-    if (s->prec == KD_FP64) k_density_x<double><<<grid_blocks(s->g.nx, 128), 128, 0, s->stream>>>((const double*)s->psi, s->g.nx, s->g.ny, dy, dst);
+    const void* st = nullptr;
+    rc = state_view(s, &st);
+    if (rc) return rc;
+    if (s->prec == KD_FP64) k_density_x<double><<<grid_blocks(s->g.nx, 128), 128, 0, s->stream>>>((const double*)st, s->g.nx, s->g.ny, dy, dst);
     else k_density_x<float><<<grid_blocks(s->g.nx, 128), 128, 0, s->stream>>>((const float*)s->psi, s->g.nx, s->g.ny, dy, dst);
     KD_CUDA(cudaGetLastError());
     ++s->launches;

@@ -68,6 +68,7 @@ struct SweepArgs {
                           // times 2^10, in the kernel's shared-memory image (32 KiB)
     const void* tc_tw;    // [1024] float2 (cos, sin) of 2 pi m / 1024
     const float* tc_scale;  // [axis][2] power-of-two operand scales, set per kd_step
+    const void* dwconst;  // double-word form: constant tables of exp and sin/cos (DWConst)
     int* status;          // error word of the simulation (KD_STATUS_* bits)
     int tc_fault;         // test hook (kd_inject_fault): the tensor-core sweep issues no
                           // matrix products, so that its bounded waits run out
@@ -85,21 +86,25 @@ constexpr int KD_STATUS_NONFINITE = 1, KD_STATUS_DRIFT = 2, KD_STATUS_TC_TIMEOUT
 // register budget is built for.  Variants that differ only in threads or tile width do
 // the same arithmetic per line (bitwise identical results); a different radix schedule,
 // or components per CTA (the compiler may fuse the pointwise ops' multiply-adds
-// differently), rounds differently.  FP64 sweeps have the one variant 0.
+// differently), rounds differently.  share (x axis, nc 2): one CTA holds both pairs of its
+// lines, the pairs' threads owning the same points; each thread evaluates the standing
+// wave for half of its points and the two halves trade the potential factors through
+// shared memory (the field costs as much as both pairs' arithmetic of the potential step).
+// FP64 sweeps have the one variant 0.
 struct SweepVariant {
-    int loge, threads, minb, nc, resident_warps;
+    int loge, threads, minb, nc, resident_warps, share;
 };
 constexpr int kNumSweepVariants = 4;
 __host__ __device__ constexpr SweepVariant sweep_variant(int axis, int v) {
     return axis == AXIS_X
-        ? (v == 1 ? SweepVariant{3, 256, 1, 2, 24}
-         : v == 2 ? SweepVariant{2, 128, 1, 2, 32}
-         : v == 3 ? SweepVariant{3, 128, 1, 4, 16}
-                  : SweepVariant{3, 128, 1, 2, 28})
-        : (v == 1 ? SweepVariant{3, 512, 8, 4, 16}
-         : v == 2 ? SweepVariant{2, 256, 4, 4, 24}
-         : v == 3 ? SweepVariant{3, 256, 4, 2, 28}
-                  : SweepVariant{3, 256, 4, 4, 16});
+        ? (v == 1 ? SweepVariant{3, 256, 1, 2, 24, 1}
+         : v == 2 ? SweepVariant{2, 128, 1, 2, 32, 0}
+         : v == 3 ? SweepVariant{3, 128, 1, 4, 16, 0}
+                  : SweepVariant{3, 128, 1, 2, 28, 0})
+        : (v == 1 ? SweepVariant{3, 512, 8, 4, 16, 0}
+         : v == 2 ? SweepVariant{2, 256, 4, 4, 24, 0}
+         : v == 3 ? SweepVariant{3, 256, 4, 2, 28, 0}
+                  : SweepVariant{3, 256, 4, 4, 16, 0});
 }
 // spinor components per CTA: FP64 CTAs own both pairs (the costly FP64 field is evaluated
 // once) except at N = 4096, where registers allow one pair
@@ -112,6 +117,11 @@ __host__ __device__ constexpr int sweep_loge(bool f64, int axis, int logn, int v
     return logn < lmax ? logn : lmax;
 }
 
+// log2 of the elements per thread of the double-word form: radix-4 stages (four
+// double-word complex values per component keep the register use within two CTAs per SM)
+// up to 1024-point lines, radix-8 above (a line's threads stay within 256)
+__host__ __device__ constexpr int sweep_loge_dw(int logn) { return logn < 2 ? logn : (logn <= 10 ? 2 : 3); }
+
 // Launches one sweep; returns cudaSuccess or the launch error.  logn in [2, 12],
 // variant in [0, kNumSweepVariants).
 template <int V>
@@ -119,6 +129,8 @@ cudaError_t launch_sweep_f32_v(int axis, int shape, int logn, const SweepArgs& a
 cudaError_t launch_sweep_f32(int variant, int axis, int shape, int logn, const SweepArgs& a,
                              cudaStream_t s);
 cudaError_t launch_sweep_f64(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
+// Double-word form (KD_DW): the FP64 form's launch shapes with every real a float pair.
+cudaError_t launch_sweep_dw(int axis, int shape, int logn, const SweepArgs& a, cudaStream_t s);
 // Precision form: whether an axis of 2^logn points has the tensor-core sweep, and its
 // launch (full sweeps only; persistent, at most two CTAs per SM).
 bool tc_supported(int logn);
@@ -127,5 +139,6 @@ cudaError_t launch_tc_sweep(int axis, const SweepArgs& a, cudaStream_t s);
 // elements (at most 2N entries of 16 B) and returns the number of entries.
 cudaError_t build_twiddles_f32(int logn, int loge, void* out, int* entries, cudaStream_t s);
 cudaError_t build_twiddles_f64(int logn, int loge, void* out, int* entries, cudaStream_t s);
+cudaError_t build_twiddles_dw(int logn, int loge, void* out, int* entries, cudaStream_t s);
 
 }  // namespace kd

@@ -1,0 +1,204 @@
+// kd_persist.cu -- the persistent form of the batched step: the Strang steps of a chunk for
+// every member of a batch (independent simulations on uneven grids, FP32) run in ONE
+// kernel launch whose CTAs pull work items from a device queue.
+//
+// Work item = (step i of the chunk, sweep y or x, member m, group g): a CTA-full of the
+// member's standalone launch blocks of that sweep (the fused y sweep with the kinetic
+// factor, the merged x sweep with the potential factor, or on the chunk's last step the
+// closing half x sweep), i.e. exactly the work the standalone kernels do, so a member
+// advanced here equals the member advanced alone with the same launch variants, bit for
+// bit.  Items are handed out in the order (i, sweep, m, g) by an atomic counter; an item
+// waits until its member has completed every item of the previous sweep (per-member
+// completion counters, acquire/release), the only dependency of a 2D FFT sweep.  Work is
+// pulled only by running CTAs and every item depends on items handed out before it, so the
+// queue always progresses without any co-residency assumption.  The waits are bounded: a
+// clock64 budget, after which the CTA sets the launch's abort flag and the members' status
+// (KD_STATUS_TC_TIMEOUT: "a bounded wait gave up"), and every CTA leaves the queue.
+#include <cuda_runtime.h>
+
+#include "kd_persist.h"
+#include "kd_sweep.cuh"
+
+namespace kd {
+
+namespace {
+
+constexpr int kThreads = 256;            // CTA size of the persistent kernel
+constexpr int kVX = 0, kVY = 3;          // launch variants of the members' sweeps
+constexpr int kMinLog = 4, kMaxLog = 9;
+
+static_assert(sizeof(SweepArgs) % sizeof(int4) == 0, "SweepArgs copies as int4");
+
+template <int LOGN, int AXIS> struct Geo {
+    static constexpr int V = AXIS == AXIS_X ? kVX : kVY;
+    using Cf = Cfg<float, LOGN, AXIS, V>;
+    static constexpr int TH = Cf::THREADS;
+    static constexpr int K = kThreads / TH;           // standalone blocks per CTA-full
+    static constexpr int SMEM = K * Cf::SMEM_BYTES;
+    static_assert(kThreads % TH == 0, "persistent CTA holds whole blocks");
+};
+
+// one item of one sweep instantiation; not inlined, so that register allocation is per
+// instantiation (one function holding every path would spill)
+template <int LOGN, int AXIS, int SHAPE>
+__device__ __noinline__ void run_group(const SweepArgs& a, int g, unsigned char* smem, int nl) {
+    using G = Geo<LOGN, AXIS>;
+    using S = Sweep<float, LOGN, AXIS, SHAPE, G::V>;
+    const int part = threadIdx.x / G::TH;
+    S::template run_block<false>(a, g * G::K + part, threadIdx.x % G::TH, smem + part * G::Cf::SMEM_BYTES, nl);
+}
+
+template <int AXIS, int SHAPE>
+__device__ __forceinline__ void run_logn(int logn, const SweepArgs& a, int g, unsigned char* smem, int nl) {
+    switch (logn) {
+        case 4: run_group<4, AXIS, SHAPE>(a, g, smem, nl); break;
+        case 5: run_group<5, AXIS, SHAPE>(a, g, smem, nl); break;
+        case 6: run_group<6, AXIS, SHAPE>(a, g, smem, nl); break;
+        case 7: run_group<7, AXIS, SHAPE>(a, g, smem, nl); break;
+        case 8: run_group<8, AXIS, SHAPE>(a, g, smem, nl); break;
+        default: run_group<9, AXIS, SHAPE>(a, g, smem, nl); break;
+    }
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// member index of item r (0 <= r < pre[n]) of a prefix-summed item count
+__device__ __forceinline__ int find_member(const int* pre, int n, int r) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_persist(const PersistPlan p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item, s_go;
+    // the item's sweep arguments, staged in shared memory (read many times by every thread)
+    __shared__ __align__(16) SweepArgs s_args;
+    const PersistMember* mem = p.members;
+    const int S = p.items_per_step;
+    const long long total = (long long)S * p.chunk;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = (int)atomicAdd(p.next, 1u);
+            s_go = s_item < total && *(volatile const int*)p.abort == 0;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (!s_go) break;
+        const int i = item / S;                 // step of the chunk, 0-based
+        int r = item % S;
+        const bool ysweep = r < p.y_items;
+        if (!ysweep) r -= p.y_items;
+        const int m = find_member(ysweep ? p.pre_y : p.pre_x, p.n, r);
+        const PersistMember& M = mem[m];
+        const int g = r - (ysweep ? p.pre_y[m] : p.pre_x[m]);
+        // dependency: every item of member m before this sweep
+        const unsigned need = (unsigned)(i * (M.iy + M.ix) + (ysweep ? 0 : M.iy));
+        if (threadIdx.x == 0) {
+            int go = 1;
+            if (ld_acquire(p.done + m) < need) {
+                const long long t0 = clock64();
+                while (ld_acquire(p.done + m) < need) {
+                    if (*(volatile const int*)p.abort) { go = 0; break; }
+                    if (clock64() - t0 > p.budget_cycles) {
+                        atomicExch(p.abort, 1);
+                        atomicOr(M.status, KD_STATUS_TC_TIMEOUT);
+                        go = 0;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+            s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const bool closing = !ysweep && i + 1 == p.chunk && p.closing;
+        {
+            const int4* src = reinterpret_cast<const int4*>(ysweep ? &M.y : (closing ? &M.xc : &M.x));
+            int4* dst = reinterpret_cast<int4*>(&s_args);
+            for (int w = threadIdx.x; w < (int)(sizeof(SweepArgs) / sizeof(int4)); w += kThreads) dst[w] = src[w];
+        }
+        __syncthreads();
+        if (ysweep) run_logn<AXIS_Y, SHAPE_F1F2>(M.ly, s_args, g, smem, 0);
+        else if (closing) run_logn<AXIS_X, SHAPE_F1>(M.lx, s_args, g, smem, i + 1);
+        else run_logn<AXIS_X, SHAPE_F1F2>(M.lx, s_args, g, smem, i + 1);
+        __syncthreads();
+        if (threadIdx.x == 0 && item != p.hold_item) {
+            __threadfence();
+            atomicAdd(p.done + m, 1u);
+        }
+    }
+}
+
+template <int LOGN> void geo_axis(int axis, int lines, int* items, int* smem) {
+    if (axis == AXIS_X) {
+        using G = Geo<LOGN, AXIS_X>;
+        const int blocks = ((lines + G::Cf::BATCH - 1) / G::Cf::BATCH) * G::Cf::NPAIRS;
+        *items = (blocks + G::K - 1) / G::K;
+        *smem = G::SMEM;
+    } else {
+        using G = Geo<LOGN, AXIS_Y>;
+        const int blocks = ((lines + G::Cf::BATCH - 1) / G::Cf::BATCH) * G::Cf::NPAIRS;
+        *items = (blocks + G::K - 1) / G::K;
+        *smem = G::SMEM;
+    }
+}
+
+template <int LOGN> int max_smem() {
+    const int a = Geo<LOGN, AXIS_X>::SMEM, b = Geo<LOGN, AXIS_Y>::SMEM;
+    return a > b ? a : b;
+}
+
+}  // namespace
+
+bool persist_supported(int logn) { return logn >= kMinLog && logn <= kMaxLog; }
+
+int persist_items(int axis, int logn, int lines) {
+    int items = 0, smem = 0;
+    switch (logn) {
+        case 4: geo_axis<4>(axis, lines, &items, &smem); break;
+        case 5: geo_axis<5>(axis, lines, &items, &smem); break;
+        case 6: geo_axis<6>(axis, lines, &items, &smem); break;
+        case 7: geo_axis<7>(axis, lines, &items, &smem); break;
+        case 8: geo_axis<8>(axis, lines, &items, &smem); break;
+        case 9: geo_axis<9>(axis, lines, &items, &smem); break;
+        default: return -1;
+    }
+    return items;
+}
+
+void persist_variants(int* vx, int* vy) { *vx = kVX; *vy = kVY; }
+
+cudaError_t launch_persist(const PersistPlan& p, cudaStream_t s) {
+    static int smem = 0, grid = 0;
+    if (grid == 0) {
+        int m = 0;
+        const int sm[] = {max_smem<4>(), max_smem<5>(), max_smem<6>(), max_smem<7>(),
+                          max_smem<8>(), max_smem<9>()};
+        for (int v : sm) m = v > m ? v : m;
+        cudaError_t e = cudaFuncSetAttribute(k_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist, kThreads, m);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        smem = m;
+        grid = per_sm * sms;
+    }
+    k_persist<<<grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace kd

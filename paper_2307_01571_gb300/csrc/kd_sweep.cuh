@@ -23,6 +23,7 @@
 
 #include <type_traits>
 
+#include "kd_dw.cuh"
 #include "kd_internal.h"
 
 namespace kd {
@@ -32,6 +33,7 @@ namespace kd {
 template <typename T> struct Cx;
 template <> struct Cx<float> { using t = float2; };
 template <> struct Cx<double> { using t = double2; };
+template <> struct Cx<DW> { using t = DWC; };
 
 template <typename C> KD_DI C mk(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
 template <typename C> KD_DI C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
@@ -67,7 +69,9 @@ template <int DIR, int S, typename C> KD_DI void dft4(C* a) {
 // radix-8 butterfly shrink the norm of two of its eight inputs by 2 h^2 - 1 (about 4e-8
 // in FP32), a bias that accumulates over thousands of steps
 template <typename T> KD_DI T mul_rsqrt2(T x) {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (std::is_same<T, DW>::value) {
+        return dw_mul(x, DW{0.707106769f, 1.21016175e-08f});
+    } else if constexpr (sizeof(T) == 4) {
         return fmaf(x, 0.707106769084930419921875f, x * 1.2101617e-08f);
     } else {
         return fma(x, 0.70710678118654757, x * -4.8336466567264567e-17);
@@ -149,34 +153,43 @@ __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
 
 template <typename T, int LOGN, int AXIS, int V> struct Cfg {
-    static constexpr bool F64 = sizeof(T) == 8;
+    static constexpr bool F64 = sizeof(T) == 8;                  // FP64 or double-word
+    static constexpr bool DWT = std::is_same<T, DW>::value;      // double-word form
     static constexpr SweepVariant VS = sweep_variant(AXIS, F64 ? 0 : V);
     static constexpr int N = 1 << LOGN;
-    static constexpr int NC = sweep_nc(F64, AXIS, LOGN, V);    // components per CTA
-    static constexpr int LOGE = sweep_loge(F64, AXIS, LOGN, V);
+    // components per thread: the double-word form keeps one pair per thread (its
+    // arithmetic needs many registers) and shares the field between the pairs of a CTA
+    static constexpr int NC = DWT ? 2 : sweep_nc(F64, AXIS, LOGN, V);
+    static constexpr int LOGE = DWT ? sweep_loge_dw(LOGN) : sweep_loge(F64, AXIS, LOGN, V);
     static constexpr int E = 1 << LOGE;                          // elements per thread
     static constexpr int TF = N / E;                             // threads per line
     // lines per CTA: rows are batched up to the variant's thread count; column tiles take
     // that many threads and at least MINB columns (FP64: 2), i.e. >= 64-128 contiguous
     // bytes per tile row, within 512 threads
     static constexpr int MINB = F64 ? 2 : VS.minb;
-    static constexpr int BATCH = AXIS == AXIS_X ? cmax(1, (F64 ? 128 : VS.threads) / TF)
+    // field sharing between the two pairs of a line (x axis, one pair per thread)
+    static constexpr bool SHARE = AXIS == AXIS_X && NC == 2 && TF <= 256 &&
+                                  (DWT || (!F64 && VS.share != 0));
+    static constexpr int PCTA = SHARE ? 2 : 1;                  // pairs per CTA (NC = 2)
+    static constexpr int BATCH = AXIS == AXIS_X ? cmax(1, (DWT ? 256 : F64 ? 128 : VS.threads) / PCTA / TF)
                                                 : (TF * MINB > 512 ? cmax(1, 512 / TF)
                                                                    : cmax(MINB, (F64 ? 256 : VS.threads) / TF));
-    static constexpr int THREADS = TF * BATCH;
+    static constexpr int THREADS = TF * BATCH * PCTA;
     static constexpr int CPP = F64 ? 1 : 2;                      // complex per 16-byte unit
     static constexpr int NPL = NC / CPP;                         // units per point in the CTA
     static constexpr int PPP = 2 / CPP;                          // units per point per pair
-    static constexpr int NPAIRS = 4 / NC;
+    static constexpr int NPAIRS = SHARE ? 1 : 4 / NC;            // CTAs per line group
     static constexpr int NST = plan_nst(LOGN, LOGE);
-    static constexpr int BUF_UNITS = BATCH * NPL * N;            // one exchange buffer
+    static constexpr int BUF_UNITS = PCTA * BATCH * NPL * N;     // one exchange buffer
     // resident CTAs per SM the FP32 sweeps are built for (the variant's resident warps;
     // the default puts the 1024x512 grid's lines in one wave); FP64 sweeps keep their full
     // register budget
-    static constexpr int MINBLK = F64 ? 1 : cmax(1, VS.resident_warps * 32 / THREADS);
+    static constexpr int MINBLK = DWT ? cmax(1, 16 * 32 / THREADS)
+                                      : (F64 ? 1 : cmax(1, VS.resident_warps * 32 / THREADS));
     // two exchange buffers (one barrier per exchange) only when they keep that occupancy
     static constexpr bool DB = 2 * BUF_UNITS * 16 * MINBLK <= 200 * 1024;
-    static constexpr int SMEM_BYTES = NST > 1 ? (DB ? 2 : 1) * BUF_UNITS * 16 : 16;
+    static constexpr int SMEM_BYTES = cmax(NST > 1 ? (DB ? 2 : 1) * BUF_UNITS * 16 : 16,
+                                           SHARE ? BATCH * N * (DWT ? 32 : 16) : 16);
     // lanes of one 8-lane (128-byte) shared-memory wavefront cover 2^LOGG consecutive
     // butterflies
     static constexpr int LOGG =
@@ -215,6 +228,69 @@ template <> struct Unit<double> {
     KD_DI static U pack(const double2* c) { return c[0]; }
     KD_DI static void unpack(U u, double2* c) { c[0] = u; }
 };
+// double-word complex: (re.h, re.l, im.h, im.l), each real in the 8 bytes a double would take
+template <> struct Unit<DW> {
+    using U = float4;
+    KD_DI static U pack(const DWC* c) { return make_float4(c[0].x.h, c[0].x.l, c[0].y.h, c[0].y.l); }
+    KD_DI static void unpack(U u, DWC* c) { c[0] = DWC{DW{u.x, u.y}, DW{u.z, u.w}}; }
+};
+
+// ------------------------------------------------- double-word potential factor ---
+// The potential factor exp(-i tau V/hbar) at one point in double-word arithmetic,
+// returned as (cos theta - 1, s a_y, s a_x) with s = sin(theta)/|a|, theta = kappa |a|:
+// the standing wave of Eqs. (Equation_of_Gaussian_beam) in product form (see
+// Sweep::op_potential_std), every quantity a double-word and exp, sin, cos of kd_dw.cuh
+// (relative error ~1e-14 of the field).  Table xtab holds per column x two double-word
+// 4-vectors (Theta0, x/(x_R w^2), w0/w, 1/w^2) and (1/w, cos zeta, sin zeta, cos k x) as
+// float4 [2][nx][2].  Not inlined: the kernels call it once per point, and one copy per
+// kernel keeps compile time and code size down.
+struct DWFactor {
+    DW c1, say, sax;
+};
+static __device__ __noinline__ DWFactor dw_potential_factor(const void* xtab_, const void* dwconst, int nx, int x,
+                                                     int kind, int longitudinal, DW y, DW y2, DW st,
+                                                     DW kap, DW e4) {
+    const DWConst* K = reinterpret_cast<const DWConst*>(dwconst);
+    const float4* xt = reinterpret_cast<const float4*>(xtab_);
+    const float4 q2 = __ldg(xt + 2 * (nx + x));       // 1/w, cos zeta
+    const float4 q3 = __ldg(xt + 2 * (nx + x) + 1);   // sin zeta, cos k x
+    DW ax = DW{0.0f, 0.0f}, ay;
+    if (kind == 1) {
+        ay = dw_scale(dw_mul(st, DW{q3.z, q3.w}), -2.0f);
+    } else {
+        const float4 q0 = __ldg(xt + 2 * x);          // Theta0, x/(x_R w^2)
+        const float4 q1 = __ldg(xt + 2 * x + 1);      // w0/w, 1/w^2
+        const DW G = dw_mul(DW{q1.x, q1.y}, dw_exp_neg(dw_mul(DW{q1.z, q1.w}, y2), K));
+        const DW th = dw_sub(DW{q0.x, q0.y}, dw_mul(DW{q0.z, q0.w}, y2));
+        DW sn, cs;
+        dw_sincos(th, K, &sn, &cs);
+        const DW sg = dw_mul(st, G);
+        ay = dw_scale(dw_mul(sg, cs), -2.0f);
+        if (longitudinal)
+            ax = dw_mul(dw_mul(e4, sg), dw_mul(dw_mul(y, DW{q2.x, q2.y}),
+                                               dw_dot2(sn, DW{q2.z, q2.w}, cs, DW{q3.x, q3.y})));
+    }
+    const DW a2 = dw_dot2(ax, ax, ay, ay);
+    const DW th2 = dw_mul(dw_mul(kap, kap), a2);
+    DW c1, s;
+    if (th2.h < 0.0625f) {
+        // Taylor series in theta^2: the terms above 1e-8 in double-word, the tails in FP32
+        const float t2 = th2.h;
+        const float tc = t2 * (-1.0f / 720 + t2 * (1.0f / 40320 + t2 * (-1.0f / 3628800)));
+        c1 = dw_mul(th2, dw_add_f(dw_mul(th2, dw_add_f(DW{4.16666679e-02f, -1.24176339e-09f}, tc)), -0.5f));
+        const float ts = t2 * (-1.0f / 5040 + t2 * (1.0f / 362880 + t2 * (-1.0f / 39916800)));
+        const DW inner = dw_add(dw_mul(th2, dw_add_f(DW{8.33333377e-03f, -4.34617218e-10f}, ts)),
+                                DW{-1.66666672e-01f, 4.96705388e-09f});
+        s = dw_mul(kap, dw_add_f(dw_mul(th2, inner), 1.0f));
+    } else {
+        const DW amag = dw_sqrt(a2);
+        DW sh, ch;
+        dw_sincos(dw_scale(dw_mul(kap, amag), 0.5f), K, &sh, &ch);
+        c1 = dw_scale(dw_mul(sh, sh), -2.0f);
+        s = dw_div(dw_scale(dw_mul(sh, ch), 2.0f), amag);
+    }
+    return DWFactor{c1, dw_mul(s, ay), dw_mul(s, ax)};
+}
 
 // ------------------------------------------------------------- the kernel ---------
 template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
@@ -222,6 +298,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
     using C = typename Cx<T>::t;
     using U = typename Unit<T>::U;
     static constexpr int N = Cf::N, E = Cf::E, TF = Cf::TF, NC = Cf::NC, NST = Cf::NST;
+    static constexpr bool DWF = std::is_same<T, DW>::value;   // double-word form
     static constexpr int NPL = Cf::NPL, CPP = Cf::CPP, BATCH = Cf::BATCH;
     // direction of the first and second FFT (forward = -1)
     static constexpr int DIR1 = AXIS == AXIS_X ? +1 : -1;
@@ -235,6 +312,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
 
     struct Ctx {
         int jt, bb, line, pair;
+        int n_local;   // step of the current kd_step call the potential factor is taken at
         bool valid;
         U* sm;
     };
@@ -313,6 +391,13 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
                             const float im = fmaf(x.x, sh, fmaf(x.y, w4.x, fmaf(x.x, sl, x.y * w4.z)));
                             b[r * NC + q] = mk<C>(re, im);
                         }
+                    } else if constexpr (DWF) {
+                        // double-word twiddle (c_hi, s_hi, c_lo, s_lo), unit modulus far
+                        // below the double-word rounding unit
+                        const float4 w4 = __ldg(reinterpret_cast<const float4*>(a.tw) + idx);
+                        const DWC w = DWC{DW{w4.x, w4.z}, DIR > 0 ? DW{-w4.y, -w4.w} : DW{w4.y, w4.w}};
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) b[r * NC + q] = dwc_mul(b[r * NC + q], w);
                     } else {
                         C w = __ldg(reinterpret_cast<const C*>(a.tw) + idx);
                         if (DIR > 0) w.y = -w.y;
@@ -412,21 +497,117 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
     // with s(t) = a0 f(t) sin(omega t + phase0) from the FP64 per-step table and the
     // x-dependent parts from the FP64 per-x table.  FP32 uses the SFU exp/sincos on
     // |Theta| <= pi + 1 (absolute error ~5e-7 of the field, no effect on unitarity).
-    KD_DI static void op_potential(const SweepArgs& a, const Ctx& c, C* v) {
+    // per-row scalars of the potential step: y of the row in the moving box and the
+    // standing wave's time factor, read (device clock, then the step's scalars) right
+    // after the grid-dependency wait so that the two dependent loads overlap the row load
+    struct RowField {
+        T y, st;
+    };
+    KD_DI static RowField row_field(const SweepArgs& a, const Ctx& c) {
+        RowField f{};
+        if (AXIS != AXIS_X || a.op != OP_POTENTIAL || a.kind == 0) return f;
+        const Clock ck = *a.clock;
+        const StepScalars* ssp = a.steps + ((ck.step - ck.base) + c.n_local);
+        if constexpr (DWF) {
+            f.y = dw_from_double(ssp->ybase + (double)c.line * a.dy);
+            f.st = dw_from_double(ssp->s);
+        } else if constexpr (sizeof(T) == 4) {
+            f.y = ssp->ybase_f + (float)c.line * a.dy_f;
+            f.st = ssp->s_f;
+        } else {
+            f.y = ssp->ybase + (double)c.line * a.dy;
+            f.st = ssp->s;
+        }
+        return f;
+    }
+
+    KD_DI static void op_potential(const SweepArgs& a, const Ctx& c, C* v, const RowField rf) {
+        if constexpr (DWF) op_potential_dw(a, c, v, rf);
+        else op_potential_std(a, c, v, rf);
+    }
+
+    // the double-word potential step: the field of the standing wave as in op_potential_std
+    // with every quantity a double-word and exp, sin, cos of kd_dw.cuh (relative error
+    // ~1e-14 of the field, so that the factor is exact to the double-word rounding unit
+    // over thousands of steps); table a.xtab holds per column x two double-word 4-vectors
+    // (Theta0, x/(x_R w^2), w0/w, 1/w^2) and (1/w, cos zeta, sin zeta, cos k x) as four
+    // float4 [2][nx][2]
+    KD_DI static void op_potential_dw(const SweepArgs& a, const Ctx& c, C* v, const RowField rf) {
+        if constexpr (DWF) {
+            if (a.kind == 0) return;
+            constexpr int R = 1 << LR_OP;
+            const DW y = rf.y, st = rf.st;
+            const DW y2 = dw_mul(y, y);
+            const DW kap = dw_from_double(a.kappa), e4 = dw_from_double(a.eps4);
+            if constexpr (!Cf::SHARE) {
+                // pairs in separate CTAs (lines of more than 256 threads): every thread
+                // evaluates the factors of all its points
+#pragma unroll
+                for (int m = 0; m < E / R; ++m)
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int x = c.jt + m * TF + r * (N / R);
+                        const DWFactor f = dw_potential_factor(a.xtab, a.dwconst, a.nx, x, a.kind,
+                                                               a.longitudinal, y, y2, st, kap, e4);
+                        apply_potential_dw(c, v + (m * R + r) * NC, f.c1, f.say, f.sax);
+                    }
+                return;
+            }
+            // the two pairs' threads own the same points: each evaluates the factors of the
+            // points of parity c.pair into shared memory, and both read all of them back
+            constexpr int SLOT = Cf::DB ? ((NST - 1) & 1) * Cf::BUF_UNITS : 0;
+            float4* fsh = reinterpret_cast<float4*>(c.sm + SLOT) + 2 * (c.bb % BATCH) * N;
+#pragma unroll
+            for (int m = 0; m < E / R; ++m)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (((m * R + r) & 1) != c.pair) continue;
+                    const int x = c.jt + m * TF + r * (N / R);
+                    const DWFactor f = dw_potential_factor(a.xtab, a.dwconst, a.nx, x, a.kind, a.longitudinal,
+                                                           y, y2, st, kap, e4);
+                    if (c.valid) {
+                        fsh[2 * x] = make_float4(f.c1.h, f.c1.l, f.say.h, f.say.l);
+                        fsh[2 * x + 1] = make_float4(f.sax.h, f.sax.l, 0.0f, 0.0f);
+                    }
+                }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E / R; ++m)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int x = c.jt + m * TF + r * (N / R);
+                    const float4 f0 = c.valid ? fsh[2 * x] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 f1 = c.valid ? fsh[2 * x + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    apply_potential_dw(c, v + (m * R + r) * NC, DW{f0.x, f0.y}, DW{f0.z, f0.w}, DW{f1.x, f1.y});
+                }
+            if constexpr (!Cf::DB) __syncthreads();
+        }
+    }
+
+    // (1 + c1) + i (s a).alpha on this thread's pair at one point, double-word: say = s a_y
+    // (negated for pair 1), sax = s a_x
+    KD_DI static void apply_potential_dw(const Ctx& c, C* e, DW c1, DW say0, DW sax) {
+        if constexpr (DWF) {
+            const DW say = c.pair == 0 ? say0 : dw_neg(say0);
+            const C u = e[0], l = e[1];
+            const C q1 = C{say, sax}, q2 = C{dw_neg(say), sax};
+            const C du = dwc_add(dwc_mul_r(u, c1), dwc_mul(l, q1));
+            const C dl = dwc_add(dwc_mul_r(l, c1), dwc_mul(u, q2));
+            e[0] = dwc_add(u, du);
+            e[1] = dwc_add(l, dl);
+        }
+    }
+
+    KD_DI static void op_potential_std(const SweepArgs& a, const Ctx& c, C* v, const RowField rf) {
         if (a.kind == 0) return;
         constexpr int R = 1 << LR_OP;
         using T4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
-        const Clock ck = *a.clock;
-        const StepScalars* ssp = a.steps + ((ck.step - ck.base) + a.n_local);
-        T y, st, kap, e4;
+        const T y = rf.y, st = rf.st;
+        T kap, e4;
         if constexpr (sizeof(T) == 4) {
-            y = ssp->ybase_f + (float)c.line * a.dy_f;
-            st = ssp->s_f;
             kap = a.kappa_f;
             e4 = a.eps4_f;
         } else {
-            y = ssp->ybase + (double)c.line * a.dy;
-            st = ssp->s;
             kap = a.kappa;
             e4 = a.eps4;
         }
@@ -434,11 +615,22 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
         const T kap2 = kap * kap;
         const T4* xt = reinterpret_cast<const T4*>(a.xtab);   // [2][nx] vectors
         const int nx = a.nx;
+        // field sharing: this thread evaluates the points e = m R + r of parity c.pair, and
+        // both pairs' threads read all factors (cos theta - 1, s a_y, s a_x) back from
+        // shared memory
+        float4* fsh = nullptr;
+        if constexpr (Cf::SHARE) {
+            constexpr int SLOT = Cf::DB ? ((NST - 1) & 1) * Cf::BUF_UNITS : 0;
+            fsh = reinterpret_cast<float4*>(c.sm + SLOT) + (c.bb % BATCH) * N;
+        }
 #pragma unroll
         for (int m = 0; m < E / R; ++m)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int x = c.jt + m * TF + r * (N / R);
+                if constexpr (Cf::SHARE) {
+                    if (((m * R + r) & 1) != c.pair) continue;
+                }
                 const T4 t1 = xt[nx + x];        // (1/w, cos zeta, sin zeta, cos k x)
                 T ax = T(0), ay;
                 if (a.kind == 1) {
@@ -468,20 +660,42 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
                     c1 = T(-2) * sh * sh;
                     s = T(2) * sh * ch / amag;
                 }
-                C* e = v + (m * R + r) * NC;
-#pragma unroll
-                for (int q = 0; q < NC / 2; ++q) {
-                    const int pr = NC == 4 ? q : c.pair;
-                    const T sg = pr == 0 ? T(1) : T(-1);
-                    const C u = e[2 * q], l = e[2 * q + 1];
-                    const C q1 = mk<C>(s * sg * ay, s * ax);
-                    const C q2 = mk<C>(-s * sg * ay, s * ax);
-                    const C du = cadd(mk<C>(c1 * u.x, c1 * u.y), cmul(q1, l));
-                    const C dl = cadd(mk<C>(c1 * l.x, c1 * l.y), cmul(q2, u));
-                    e[2 * q] = cadd(u, du);
-                    e[2 * q + 1] = cadd(l, dl);
+                if constexpr (Cf::SHARE) {
+                    if (c.valid) fsh[x] = make_float4(c1, s * ay, s * ax, 0.0f);
+                } else {
+                    apply_potential(c, v + (m * R + r) * NC, c1, s * ay, s * ax);
                 }
             }
+        if constexpr (Cf::SHARE) {
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E / R; ++m)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int x = c.jt + m * TF + r * (N / R);
+                    const float4 f = c.valid ? fsh[x] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    apply_potential(c, v + (m * R + r) * NC, f.x, f.y, f.z);
+                }
+            // single buffer: the next exchange writes over the factors
+            if constexpr (!Cf::DB) __syncthreads();
+        }
+    }
+
+    // (1 + c1) + i (s a).alpha on the pairs of one point: say = s a_y, sax = s a_x (pair 1's
+    // generator has a_y negated)
+    KD_DI static void apply_potential(const Ctx& c, C* e, T c1, T say, T sax) {
+#pragma unroll
+        for (int q = 0; q < NC / 2; ++q) {
+            const int pr = NC == 4 ? q : c.pair;
+            const T sy = pr == 0 ? say : -say;
+            const C u = e[2 * q], l = e[2 * q + 1];
+            const C q1 = mk<C>(sy, sax);
+            const C q2 = mk<C>(-sy, sax);
+            const C du = cadd(mk<C>(c1 * u.x, c1 * u.y), cmul(q1, l));
+            const C dl = cadd(mk<C>(c1 * l.x, c1 * l.y), cmul(q2, u));
+            e[2 * q] = cadd(u, du);
+            e[2 * q + 1] = cadd(l, dl);
+        }
     }
 
     // kinetic factor e^{i phi} [C - i S H0(pi)] / P on registers; element index is k_y,
@@ -500,11 +714,67 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int ky = c.jt + m * TF + r * (N / R);
-                kab[m * R + r] = c.valid ? __ldcg(kt + (long long)ky * a.nx + c.line) : mk<C>(T(0), T(0));
+                if constexpr (DWF) {
+                    const float4 q = c.valid ? __ldcg(reinterpret_cast<const float4*>(a.ktab) + (long long)ky * a.nx + c.line)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                    kab[m * R + r] = DWC{DW{q.x, q.y}, DW{q.z, q.w}};
+                } else {
+                    kab[m * R + r] = c.valid ? __ldcg(kt + (long long)ky * a.nx + c.line) : mk<C>(T(0), T(0));
+                }
             }
     }
 
     KD_DI static void op_kinetic(const SweepArgs& a, const Ctx& c, C* v, const C* kab) {
+        if constexpr (DWF) op_kinetic_dw(a, c, v, kab);
+        else op_kinetic_std(a, c, v, kab);
+    }
+
+    // the double-word kinetic step, the same factor as op_kinetic_std: tables a.kxtab
+    // [nx] double-word pi_x (float2), a.kytab [ny][2] float4 (pi_y, cos phi - 1 | sin phi),
+    // a.ktab [ny][nx] float4 ((C - 1)/P, c S/P)
+    KD_DI static void op_kinetic_dw(const SweepArgs& a, const Ctx& c, C* v, const C* kab) {
+        if constexpr (DWF) {
+            constexpr int R = 1 << LR_OP;
+            const float2 px = __ldg(reinterpret_cast<const float2*>(a.kxtab) + c.line);
+            const DW pix = DW{px.x, px.y};
+            const DW mc = dw_from_double(a.mc);
+            const float invP = (float)a.invP;   // a power of two: exact
+            const float4* kyt = reinterpret_cast<const float4*>(a.kytab);
+#pragma unroll
+            for (int m = 0; m < E / R; ++m)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int ky = c.jt + m * TF + r * (N / R);
+                    const C ab = kab[m * R + r];
+                    const float4 y0 = __ldg(kyt + 2 * ky), y1 = __ldg(kyt + 2 * ky + 1);
+                    const DW fx = DW{y0.z, y0.w}, fy = DW{y1.x, y1.y};
+                    C* e = v + (m * R + r) * NC;
+#pragma unroll
+                    for (int q = 0; q < NC / 2; ++q) {
+                        const int pr = NC == 4 ? q : c.pair;
+                        const DW piy = pr == 0 ? DW{y0.x, y0.y} : DW{-y0.x, -y0.y};
+                        const C u = e[2 * q], l = e[2 * q + 1];
+                        // G = H0/c on the pair: (mc u + (pix - i piy) l, (pix + i piy) u - mc l)
+                        const C hu = C{dw_add(dw_dot2(mc, u.x, pix, l.x), dw_mul(piy, l.y)),
+                                       dw_sub(dw_dot2(mc, u.y, pix, l.y), dw_mul(piy, l.x))};
+                        const C hl = C{dw_sub(dw_dot2(pix, u.x, piy, dw_neg(u.y)), dw_mul(mc, l.x)),
+                                       dw_sub(dw_dot2(pix, u.y, piy, u.x), dw_mul(mc, l.y))};
+                        // u/P + a u - i b hu
+                        const C u1 = C{dw_add(dw_scale(u.x, invP), dw_dot2(ab.x, u.x, ab.y, hu.y)),
+                                       dw_add(dw_scale(u.y, invP), dw_dot2(ab.x, u.y, dw_neg(ab.y), hu.x))};
+                        const C l1 = C{dw_add(dw_scale(l.x, invP), dw_dot2(ab.x, l.x, ab.y, hl.y)),
+                                       dw_add(dw_scale(l.y, invP), dw_dot2(ab.x, l.y, dw_neg(ab.y), hl.x))};
+                        // times 1 + f (frame translation phase)
+                        e[2 * q] = C{dw_add(u1.x, dw_dot2(fx, u1.x, dw_neg(fy), u1.y)),
+                                     dw_add(u1.y, dw_dot2(fx, u1.y, fy, u1.x))};
+                        e[2 * q + 1] = C{dw_add(l1.x, dw_dot2(fx, l1.x, dw_neg(fy), l1.y)),
+                                         dw_add(l1.y, dw_dot2(fx, l1.y, fy, l1.x))};
+                    }
+                }
+        }
+    }
+
+    KD_DI static void op_kinetic_std(const SweepArgs& a, const Ctx& c, C* v, const C* kab) {
         constexpr int R = 1 << LR_OP;
         const T pix = __ldg(reinterpret_cast<const T*>(a.kxtab) + c.line);
         T mc, invP;   // invP = 1/P is exact (power of two)
@@ -543,23 +813,36 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
 
     KD_DI static void run(const SweepArgs& a) {
         extern __shared__ __align__(16) unsigned char smem_raw[];
+        run_block<true>(a, (int)blockIdx.x, (int)threadIdx.x, smem_raw, a.n_local);
+    }
+
+    // One launch block `blk` of the sweep, executed by the THREADS threads tid = 0..THREADS-1
+    // with `smem` (SMEM_BYTES) as its shared memory.  PDL: a standalone launch waits for the
+    // previous grid here; the persistent batch kernel (kd_persist.cu) runs blocks as work
+    // items after its own dependency wait (every thread of the CTA reaches the same
+    // barriers: items of one kind run side by side with the same instantiation).
+    template <bool PDL>
+    KD_DI static void run_block(const SweepArgs& a, int blk, int tid, unsigned char* smem, int n_local) {
         Ctx c;
-        const int tid = threadIdx.x;
+        c.n_local = n_local;
         if (AXIS == AXIS_X) { c.bb = tid / TF; c.jt = tid % TF; }
         else { c.bb = tid % BATCH; c.jt = tid / BATCH; }
-        // the pair index varies fastest so both pairs of a line tile run together
-        c.pair = NC == 2 ? (int)(blockIdx.x % Cf::NPAIRS) : 0;
-        c.line = (int)(blockIdx.x / Cf::NPAIRS) * BATCH + c.bb;
+        // the pair index varies fastest so both pairs of a line tile run together; with
+        // field sharing both pairs are in the CTA (c.bb then counts PCTA x BATCH lines)
+        if constexpr (Cf::SHARE) c.pair = c.bb / BATCH;
+        else c.pair = NC == 2 ? blk % Cf::NPAIRS : 0;
+        c.line = (blk / Cf::NPAIRS) * BATCH + c.bb % BATCH;
         c.valid = c.line < (AXIS == AXIS_X ? a.ny : a.nx);
-        c.sm = reinterpret_cast<U*>(smem_raw);
+        c.sm = reinterpret_cast<U*>(smem);
         C v[E * NC];
         // programmatic dependent launch: everything above ran while the previous kernel
         // in the stream was still finishing; its results are visible after this wait
         // (a hardware-managed wait for the prerequisite grid, not a spin loop)
-        asm volatile("griddepcontrol.wait;" ::: "memory");
+        if constexpr (PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
+        const RowField rf = row_field(a, c);
         load<LR_LOAD>(a, c, v);
         // the next kernel may start its own prologue as our CTAs retire
-        asm volatile("griddepcontrol.launch_dependents;");
+        if constexpr (PDL) asm volatile("griddepcontrol.launch_dependents;");
         if constexpr (AXIS == AXIS_Y) {
             C kab[E];
             if (a.op == OP_KINETIC) load_ktab(a, c, kab);
@@ -567,9 +850,10 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
             if (a.op == OP_KINETIC) op_kinetic(a, c, v, kab);
         } else {
             if constexpr (HAS1) fft<DIR1, false, 0, 0>(a, c, v);
-            if (a.op == OP_POTENTIAL) op_potential(a, c, v);
+            if (a.op == OP_POTENTIAL) op_potential(a, c, v, rf);
         }
-        if constexpr (HAS2) fft<DIR2, true, HAS1 ? NST - 1 : 0, 0>(a, c, v);
+        // with field sharing the factor trade takes exchange slot NST - 1, so FFT2 starts at NST
+        if constexpr (HAS2) fft<DIR2, true, Cf::SHARE ? NST : (HAS1 ? NST - 1 : 0), 0>(a, c, v);
         store<LR_STORE>(a, c, v);
     }
 };
@@ -632,7 +916,34 @@ __global__ void twiddle_kernel(void* out) {
         double sn, cs;
         sincospi(2.0 * (double)(r * k) / (double)(ns << lr), &sn, &cs);
         sn = -sn;
-        if constexpr (sizeof(T) == 4) {
+        if constexpr (std::is_same<T, DW>::value) {
+            // double-word entries (c_hi, s_hi, c_lo, s_lo): among the lo parts within 3 FP32
+            // steps of the rounded residuals, the pair whose represented (C, S) has
+            // C^2 + S^2 closest to 1 (evaluated exactly with FP64 TwoProd/TwoSum), with a
+            // small weight on the distance to (cos, sin): a twiddle of modulus 1 + d would
+            // change the norm by 2 d at every product, coherently over the steps of a run
+            const float ch = (float)cs, sh = (float)sn;
+            const float cl0 = (float)(cs - (double)ch), sl0 = (float)(sn - (double)sh);
+            float bc = cl0, bs = sl0;
+            double best = 1e300;
+            float ci = cl0;
+            for (int q = 0; q < 3; ++q) ci = nextafterf(ci, -INFINITY);
+            for (int i = 0; i < 7; ++i, ci = nextafterf(ci, INFINITY)) {
+                float si = sl0;
+                for (int q = 0; q < 3; ++q) si = nextafterf(si, -INFINITY);
+                for (int j = 0; j < 7; ++j, si = nextafterf(si, INFINITY)) {
+                    const double C = (double)ch + (double)ci, S = (double)sh + (double)si;
+                    const double pc = C * C, ec = fma(C, C, -pc);
+                    const double ps = S * S, es = fma(S, S, -ps);
+                    const double hi = pc + ps, bb = hi - pc;
+                    const double lo = (pc - (hi - bb)) + (ps - bb);
+                    const double d = ((hi - 1.0) + lo) + (ec + es);
+                    const double g = fabs(d) + 0.05 * (fabs(C - cs) + fabs(S - sn));
+                    if (g < best) { best = g; bc = ci; bs = si; }
+                }
+            }
+            reinterpret_cast<float4*>(out)[e] = make_float4(ch, sh, bc, bs);
+        } else if constexpr (sizeof(T) == 4) {
             const float ch = (float)cs, sh = (float)sn;
             reinterpret_cast<float4*>(out)[e] = make_float4(ch, sh, (float)(cs - (double)ch), (float)(sn - (double)sh));
         } else {

@@ -22,10 +22,11 @@ KD_OK = 0
 KD_ERR_ARG, KD_ERR_UNSUPPORTED_SIZE, KD_ERR_CUDA = -1, -2, -3
 KD_ERR_NONFINITE, KD_ERR_NORM_DRIFT, KD_ERR_TIMEOUT = -4, -5, -6
 KD_ERR_STATE_MISMATCH, KD_ERR_NOMEM, KD_ERR_CANCELLED = -7, -8, -9
-KD_FP64, KD_FP32, KD_FP32_TC = 0, 1, 2
+KD_FP64, KD_FP32, KD_FP32_TC, KD_DW = 0, 1, 2, 3
 KD_HOST, KD_DEVICE = 0, 1
 KD_SWEEP_VARIANTS, KD_TUNE_FORCE = 4, 1
-KD_FAULT_TC_WAIT = 1
+KD_FAULT_TC_WAIT, KD_FAULT_PERSIST_HOLD = 1, 2
+KD_BATCH_GRAPH, KD_BATCH_PERSISTENT = 0, 1
 
 
 class KdError(RuntimeError):
@@ -117,6 +118,7 @@ _SIGS = {
                                 _P(C.c_int64)]),
     "kd_batch_destroy": (None, [_vp]),
     "kd_batch_autotune": (C.c_int, [_vp, _P(C.c_double), C.c_int32, _P(C.c_int32)]),
+    "kd_batch_set_mode": (C.c_int, [_vp, C.c_int32]),
     "kd_mlp_create": (C.c_int, [_P(C.c_int32), C.c_int32, _P(_vp)]),
     "kd_mlp_num_params": (C.c_int, [_vp, _P(C.c_int64)]),
     "kd_mlp_set_params": (C.c_int, [_vp, _vp, C.c_int32]),
@@ -167,7 +169,7 @@ class Sim:
     def __init__(self, units: W.Units, grid: W.Grid, field: W.Field, precision: int = KD_FP64,
                  stream: int | None = None):
         self.units, self.grid, self.field, self.precision = units, grid, field, precision
-        self.cdtype = np.complex128 if precision == KD_FP64 else np.complex64
+        self.cdtype = np.complex128 if precision in (KD_FP64, KD_DW) else np.complex64
         h = _vp()
         _check(kd_create(C.byref(_fill(kd_units, units)), C.byref(_fill(kd_grid, grid)),
                          C.byref(_fill(kd_field, field)), precision,
@@ -297,8 +299,10 @@ class Sim:
         _check(kd_set_sweep_variants(self._h, int(v[0]), int(v[1])))
 
     def inject_fault(self, kind: int = KD_FAULT_TC_WAIT):
-        """Test hook (``kd_inject_fault``): the next ``step`` call's tensor-core sweeps issue
-        no matrix products, so their bounded waits run out and ``step`` raises KD_ERR_TIMEOUT."""
+        """Test hooks (``kd_inject_fault``): KD_FAULT_TC_WAIT -- the next ``step`` call's
+        tensor-core sweeps issue no matrix products, so their bounded waits run out and
+        ``step`` raises KD_ERR_TIMEOUT; KD_FAULT_PERSIST_HOLD -- in the next persistent
+        batch step the completion of this member's first work item is never signalled."""
         _check(kd_inject_fault(self._h, kind))
 
     def launch_count(self) -> int:
@@ -345,6 +349,11 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_mode(self, mode: int):
+        """KD_BATCH_GRAPH (graph branches) or KD_BATCH_PERSISTENT (one persistent kernel per
+        chunk with a device work queue) -- ``kd_batch_set_mode``."""
+        _check(kd_batch_set_mode(self._h, mode))
 
     def autotune(self, dts, steps: int = 20) -> list:
         """Launch variants timed on the whole batch (``kd_batch_autotune``); the members'

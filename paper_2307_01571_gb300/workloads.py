@@ -18,7 +18,7 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 NONE, PLANE, GAUSS = 0, 1, 2
-FP64, FP32, FP32_TC = 0, 1, 2
+FP64, FP32, FP32_TC, DW = 0, 1, 2, 3
 
 
 @dataclass(frozen=True)
@@ -155,7 +155,7 @@ def c2(units: Units = ATOMIC, w0_lambda: float = 10.0, longitudinal: int = 1,
     f = Field(kind=GAUSS, longitudinal=longitudinal, a0=0.1, k_L=k, epsilon=eps, env_T=0.0,
               p_shift_x=0.0, p_shift_y=units.mc, box_vy=units.c / math.sqrt(2.0))
     p = Packet(-units.hbar * k, units.mc, 0.0, 0.0, units.hbar * k / 20.0, 1, 0)
-    tag = "c128" if precision == FP64 else "c64"
+    tag = {FP64: "c128", DW: "c128 as double-word FP32 pairs"}.get(precision, "c64")
     return Workload(f"Gaussian-beam standing wave 1024x512 {tag}, w0={w0_lambda:g} lambda, "
                     f"{nsteps} steps", units, g, f, p, dt, nsteps, obs_every=100,
                     precision=precision)

@@ -5,6 +5,7 @@ by one with kd_step, which the parity tests check against the oracle."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2307_01571_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -98,3 +99,97 @@ def test_batch_autotune_keeps_states_and_steps_like_members_alone(kd):
             alone.set_state(blob)         # the member's state and clock before the batch
             alone.step(wl.dt, 20)
             assert np.array_equal(alone.get_spinor(), got)
+
+
+# ------------------------------------------------------------ persistent form
+PERSIST_VARIANTS = (0, 3)
+
+
+def _mixed_members():
+    return [W.small(128, 64, W.GAUSS, units=W.ATOMIC, a0=0.3),
+            W.small(64, 256, W.GAUSS, units=W.ATOMIC, a0=0.2),
+            W.small(32, 32, W.PLANE, units=W.ATOMIC, a0=0.4),
+            W.small(512, 128, W.GAUSS, units=W.ATOMIC, a0=0.1),
+            W.small(16, 512, W.NONE, units=W.ATOMIC)]
+
+
+def test_persistent_batch_equals_members_alone(kd):
+    """One persistent kernel per chunk (device work queue, per-member completion counters)
+    advances every member exactly as its own sweeps would: bitwise equal to the members
+    run alone on the same launch variants, over chunks with observations and two calls."""
+    wls = _mixed_members()
+    alone, alone_obs = [], []
+    for wl in wls:
+        with kd.Sim.from_workload(wl.with_(precision=1)) as sim:
+            sim.sweep_variants = PERSIST_VARIANTS
+            sim.init_packet(wl.packet)
+            o1 = sim.step(wl.dt, 45, obs_every=15)
+            o2 = sim.step(wl.dt, 30, obs_every=15)
+            alone.append(sim.get_spinor())
+            alone_obs.append(o1 + o2)
+    sims = [kd.Sim.from_workload(wl.with_(precision=1)) for wl in wls]
+    for s, wl in zip(sims, wls):
+        s.init_packet(wl.packet)
+    with kd.Batch(sims) as b:
+        b.set_mode(kd.KD_BATCH_PERSISTENT)
+        o1 = b.step([wl.dt for wl in wls], 45, obs_every=15)
+        o2 = b.step([wl.dt for wl in wls], 30, obs_every=15)
+    for i, s in enumerate(sims):
+        assert np.array_equal(s.get_spinor(), alone[i]), i
+        assert o1[i] + o2[i] == alone_obs[i], i
+        assert s.get_time()[1] == 75
+        s.close()
+
+
+def test_persistent_batch_against_oracle(kd):
+    wl = W.small(64, 32, W.GAUSS, units=W.ATOMIC, a0=0.4, nsteps=6)
+    psi = W.random_spinor(64, 32, 77)
+    ref = oracle.step(wl.units, wl.grid, wl.field, psi, 0.0, wl.dt, 6)
+    sims = [kd.Sim.from_workload(wl.with_(precision=1)), kd.Sim.from_workload(wl.with_(precision=1))]
+    for s in sims:
+        s.set_spinor(psi)
+    with kd.Batch(sims) as b:
+        b.set_mode(kd.KD_BATCH_PERSISTENT)
+        b.step([wl.dt, wl.dt], 6)
+    for s in sims:
+        got = s.get_spinor().astype(np.complex128)
+        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+        s.close()
+
+
+def test_persistent_batch_withheld_producer_times_out(kd):
+    """A member's first work item never signals completion (test hook): the items waiting
+    for it give up after their bounded waits, the call returns KD_ERR_TIMEOUT, and the
+    context stays usable."""
+    wls = [W.small(64, 64, W.GAUSS, units=W.ATOMIC), W.small(128, 32, W.GAUSS, units=W.ATOMIC)]
+    sims = [kd.Sim.from_workload(wl.with_(precision=1)) for wl in wls]
+    for s, wl in zip(sims, wls):
+        s.init_packet(wl.packet)
+    with kd.Batch(sims) as b:
+        b.set_mode(kd.KD_BATCH_PERSISTENT)
+        sims[1].inject_fault(kd.KD_FAULT_PERSIST_HOLD)
+        with pytest.raises(kd.KdError) as e:
+            b.step([wl.dt for wl in wls], 10)
+        assert e.value.code == kd.KD_ERR_TIMEOUT
+        # the hook lasted one call: fresh states step correctly afterwards
+        for s, wl in zip(sims, wls):
+            s.init_packet(wl.packet)
+        b.step([wl.dt for wl in wls], 10)
+    for s, wl in zip(sims, wls):
+        with kd.Sim.from_workload(wl.with_(precision=1)) as alone:
+            alone.sweep_variants = PERSIST_VARIANTS
+            alone.init_packet(wl.packet)
+            alone.step(wl.dt, 10)
+            assert np.array_equal(alone.get_spinor(), s.get_spinor())
+        s.close()
+
+
+def test_persistent_batch_rejects_unsupported_members(kd):
+    for wl, prec in [(W.small(64, 64, W.GAUSS), 0), (W.small(1024, 64, W.GAUSS), 1),
+                     (W.small(64, 64, W.GAUSS), 2)]:
+        sims = [kd.Sim.from_workload(wl.with_(precision=prec))]
+        with kd.Batch(sims) as b:
+            with pytest.raises(kd.KdError) as e:
+                b.set_mode(kd.KD_BATCH_PERSISTENT)
+            assert e.value.code == kd.KD_ERR_UNSUPPORTED_SIZE
+        sims[0].close()

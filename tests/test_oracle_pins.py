@@ -538,3 +538,19 @@ def test_packet_position_phase_translates_exactly():
     pa = oracle.init_packet(NAT, g, f, a)
     pb = oracle.init_packet(NAT, g, f, b)
     assert np.max(np.abs(pb - np.roll(pa, (my, mx), axis=(0, 1)))) < 1e-12 * np.max(np.abs(pa))
+
+
+def test_study_definitions():
+    from paper_2307_01571_gb300 import studies
+    w3, w4 = studies.e3(), studies.e4()
+    assert len(w3) == 12 and len(w4) == 8
+    for w in w3:
+        e, kn = w.extra["eps"], w.extra["k_nat"]
+        lam = 2 * math.pi / w.field.k_L
+        assert abs(w.field.k_L - kn) < 1e-15 and abs(w.field.epsilon - e) < 1e-15
+        assert abs((w.grid.x_max - w.grid.x_min) - 80 * lam) < 1e-9 * lam
+        assert abs(w.nsteps * w.dt - 280 * lam * math.sqrt(2)) < w.dt
+    assert sorted({w.field.longitudinal for w in w4}) == [0, 1]
+    # the slope fit recovers an exact power law
+    x = np.array([1.0, 2.0, 5.0, 10.0])
+    assert abs(studies.fit_slope(x, 3.0 * x ** 2) - 2.0) < 1e-12
