@@ -228,6 +228,9 @@ void kd_batch_destroy(kd_batch* batch);
  * (may be NULL) receives 2 ints per member (x, y).  steps in [1, 4096]; synchronises;
  * KD_ERR_ARG while the batch's or a member's stream is being captured. */
 int kd_batch_autotune(kd_batch* batch, const double* dt, int32_t steps, int32_t* variants);
+/* (In the persistent form, kd_batch_set_mode below, the x variants are searched among the two the
+ * persistent kernel holds, and the work item size, 1, 2 or 4 CTA-fulls of blocks, is tuned
+ * the same way.) */
 
 /* Persistent form of the batch (KD_BATCH_PERSISTENT): each chunk of steps of all members
  * runs as ONE kernel launch whose CTAs pull work items (step, sweep, member, group of
@@ -237,9 +240,10 @@ int kd_batch_autotune(kd_batch* batch, const double* dt, int32_t steps, int32_t*
  * KD_ERR_TIMEOUT (the members' states are then not valid evolutions).  The observation and
  * opening-half work at chunk ends runs as graph branches beside it, and the whole chunk is
  * one CUDA-graph launch.  Every member must be KD_FP32 with both axes of 16 ... 512 points
- * (else KD_ERR_UNSUPPORTED_SIZE); the members' sweeps run launch variants (x 0, y 3), and a
- * member advanced this way equals the member advanced alone on those variants, bit for
- * bit.  KD_BATCH_GRAPH (the default) restores the graph-branch form.  The persistent form
+ * (else KD_ERR_UNSUPPORTED_SIZE).  The kernel holds launch variants x 0 and 2 and y 3: a
+ * member's x sweep runs its own variant when it is 2 (as kd_autotune picks for small
+ * grids), else 0; its y sweep runs 3.  A member advanced this way equals the member
+ * advanced alone on those variants, bit for bit.  KD_BATCH_GRAPH (the default) restores the graph-branch form.  The persistent form
  * holds device buffers of its own (descriptors and counters, O(n)).  Synchronises. */
 #define KD_BATCH_GRAPH 0
 #define KD_BATCH_PERSISTENT 1

@@ -1765,6 +1765,7 @@ struct kd_batch {
     int* d_abort = nullptr;
     int y_items = 0, x_items = 0;
     int hold_item = -1;              // withheld completion of the current step call (test hook)
+    int persist_group = 1;           // CTA-fulls per work item (kd_batch_autotune)
 };
 
 namespace {
@@ -1785,8 +1786,16 @@ int persist_upload(kd_batch* b, const std::vector<StepPlan>& plans, bool* hold) 
         m.xc = make_args(s, AXIS_X, OP_POTENTIAL, s->psi, s->psi, 0, 0.5 * plans[i].dt, false);
         m.lx = s->lx;
         m.ly = s->ly;
-        m.iy = persist_items(AXIS_Y, s->ly, s->g.nx);
-        m.ix = persist_items(AXIS_X, s->lx, s->g.ny);
+        // the member's own launch variants where the kernel holds them, else its defaults;
+        // the same number of CTA-fulls per work item for every member (uneven groups let
+        // the large members' items set the pace of every sweep)
+        m.vx_alt = persist_variant_alt(AXIS_X, s->var[AXIS_X]);
+        m.vy_alt = persist_variant_alt(AXIS_Y, s->var[AXIS_Y]);
+        m.cy = persist_ctas(AXIS_Y, m.vy_alt, s->ly, s->g.nx);
+        m.cx = persist_ctas(AXIS_X, m.vx_alt, s->lx, s->g.ny);
+        m.gy = m.gx = b->persist_group;
+        m.iy = (m.cy + m.gy - 1) / m.gy;
+        m.ix = (m.cx + m.gx - 1) / m.gx;
         m.status = s->status;
         pre[i + 1] = pre[i] + m.iy;
         pre[n + 1 + i + 1] = pre[n + 1 + i] + m.ix;
@@ -2120,6 +2129,11 @@ int kd_batch_autotune(kd_batch* b, const double* dt, int32_t steps, int32_t* var
             float best_ms = base;
             for (int v = 0; v < KD_SWEEP_VARIANTS && !rc; ++v) {
                 if (v == cur) continue;
+                if (b->persistent) {   // the persistent kernel holds x variants 0 and 2 only
+                    int v0, v1;
+                    persist_variants(ax, &v0, &v1);
+                    if (v != v0 && v != v1) continue;
+                }
                 for (size_t i : kv.second) set_var(i, ax, v);
                 float ms = 0.0f;
                 rc = timed(&ms);
@@ -2128,6 +2142,23 @@ int kd_batch_autotune(kd_batch* b, const double* dt, int32_t steps, int32_t* var
             for (size_t i : kv.second) set_var(i, ax, best);
             base = best_ms;
         }
+    // persistent form: the work item size (CTA-fulls per item), same rule
+    if (b->persistent && !rc) {
+        int best = b->persist_group;
+        float best_ms = base;
+        for (int g : {1, 2, 4}) {
+            if (g == b->persist_group || rc) continue;
+            const int cur = b->persist_group;
+            b->persist_group = g;
+            clear_batch_graphs(b);
+            float ms = 0.0f;
+            rc = timed(&ms);
+            b->persist_group = cur;
+            if (!rc && ms < 0.98f * best_ms) { best = g; best_ms = ms; }
+        }
+        b->persist_group = best;
+        clear_batch_graphs(b);
+    }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     // states and clocks back (whatever happened above)

@@ -24,13 +24,15 @@ namespace kd {
 namespace {
 
 constexpr int kThreads = 256;            // CTA size of the persistent kernel
-constexpr int kVX = 0, kVY = 3;          // launch variants of the members' sweeps
+// launch variants the kernel holds per axis: x radix-8 (default) and radix-4 Stockham
+// stages; y one variant (the radix-4 y variant needs 512-thread CTAs at 512 points)
+constexpr int kVX0 = 0, kVX1 = 2, kVY0 = 3;
 constexpr int kMinLog = 4, kMaxLog = 9;
 
 static_assert(sizeof(SweepArgs) % sizeof(int4) == 0, "SweepArgs copies as int4");
 
-template <int LOGN, int AXIS> struct Geo {
-    static constexpr int V = AXIS == AXIS_X ? kVX : kVY;
+template <int LOGN, int AXIS, int VAR> struct Geo {
+    static constexpr int V = VAR;
     using Cf = Cfg<float, LOGN, AXIS, V>;
     static constexpr int TH = Cf::THREADS;
     static constexpr int K = kThreads / TH;           // standalone blocks per CTA-full
@@ -40,23 +42,35 @@ template <int LOGN, int AXIS> struct Geo {
 
 // one item of one sweep instantiation; not inlined, so that register allocation is per
 // instantiation (one function holding every path would spill)
-template <int LOGN, int AXIS, int SHAPE>
+template <int LOGN, int AXIS, int SHAPE, int VAR>
 __device__ __noinline__ void run_group(const SweepArgs& a, int g, unsigned char* smem, int nl) {
-    using G = Geo<LOGN, AXIS>;
+    using G = Geo<LOGN, AXIS, VAR>;
     using S = Sweep<float, LOGN, AXIS, SHAPE, G::V>;
     const int part = threadIdx.x / G::TH;
     S::template run_block<false>(a, g * G::K + part, threadIdx.x % G::TH, smem + part * G::Cf::SMEM_BYTES, nl);
 }
 
-template <int AXIS, int SHAPE>
-__device__ __forceinline__ void run_logn(int logn, const SweepArgs& a, int g, unsigned char* smem, int nl) {
+template <int AXIS, int SHAPE, int VAR>
+__device__ __forceinline__ void run_logn_v(int logn, const SweepArgs& a, int g, unsigned char* smem, int nl) {
     switch (logn) {
-        case 4: run_group<4, AXIS, SHAPE>(a, g, smem, nl); break;
-        case 5: run_group<5, AXIS, SHAPE>(a, g, smem, nl); break;
-        case 6: run_group<6, AXIS, SHAPE>(a, g, smem, nl); break;
-        case 7: run_group<7, AXIS, SHAPE>(a, g, smem, nl); break;
-        case 8: run_group<8, AXIS, SHAPE>(a, g, smem, nl); break;
-        default: run_group<9, AXIS, SHAPE>(a, g, smem, nl); break;
+        case 4: run_group<4, AXIS, SHAPE, VAR>(a, g, smem, nl); break;
+        case 5: run_group<5, AXIS, SHAPE, VAR>(a, g, smem, nl); break;
+        case 6: run_group<6, AXIS, SHAPE, VAR>(a, g, smem, nl); break;
+        case 7: run_group<7, AXIS, SHAPE, VAR>(a, g, smem, nl); break;
+        case 8: run_group<8, AXIS, SHAPE, VAR>(a, g, smem, nl); break;
+        default: run_group<9, AXIS, SHAPE, VAR>(a, g, smem, nl); break;
+    }
+}
+
+// alt selects the second variant of the axis
+template <int AXIS, int SHAPE>
+__device__ __forceinline__ void run_logn(int logn, int alt, const SweepArgs& a, int g, unsigned char* smem, int nl) {
+    if constexpr (AXIS == AXIS_X) {
+        if (alt) run_logn_v<AXIS, SHAPE, kVX1>(logn, a, g, smem, nl);
+        else run_logn_v<AXIS, SHAPE, kVX0>(logn, a, g, smem, nl);
+    } else {
+        (void)alt;   // one y variant
+        run_logn_v<AXIS, SHAPE, kVY0>(logn, a, g, smem, nl);
     }
 }
 
@@ -84,10 +98,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const PersistPlan p) {
     const PersistMember* mem = p.members;
     const int S = p.items_per_step;
     const long long total = (long long)S * p.chunk;
+    // thread 0 takes the next item from the queue while the CTA works on the current one
+    int next_item = 0;
+    if (threadIdx.x == 0) next_item = (int)atomicAdd(p.next, 1u);
     for (;;) {
         if (threadIdx.x == 0) {
-            s_item = (int)atomicAdd(p.next, 1u);
-            s_go = s_item < total && *(volatile const int*)p.abort == 0;
+            s_item = next_item;
+            s_go = next_item < total && *(volatile const int*)p.abort == 0;
+            if (s_go) next_item = (int)atomicAdd(p.next, 1u);
         }
         __syncthreads();
         const int item = s_item;
@@ -127,55 +145,73 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const PersistPlan p) {
             for (int w = threadIdx.x; w < (int)(sizeof(SweepArgs) / sizeof(int4)); w += kThreads) dst[w] = src[w];
         }
         __syncthreads();
-        if (ysweep) run_logn<AXIS_Y, SHAPE_F1F2>(M.ly, s_args, g, smem, 0);
-        else if (closing) run_logn<AXIS_X, SHAPE_F1>(M.lx, s_args, g, smem, i + 1);
-        else run_logn<AXIS_X, SHAPE_F1F2>(M.lx, s_args, g, smem, i + 1);
+        // the item's CTA-fulls of blocks, one after the other (a barrier between them, so
+        // that no thread writes shared memory another still reads)
+        const int per = ysweep ? M.gy : M.gx, nct = ysweep ? M.cy : M.cx;
+        const int c0 = g * per, c1 = c0 + per < nct ? c0 + per : nct;
+        for (int cf = c0; cf < c1; ++cf) {
+            if (cf > c0) __syncthreads();
+            if (ysweep) run_logn<AXIS_Y, SHAPE_F1F2>(M.ly, M.vy_alt, s_args, cf, smem, 0);
+            else if (closing) run_logn<AXIS_X, SHAPE_F1>(M.lx, M.vx_alt, s_args, cf, smem, i + 1);
+            else run_logn<AXIS_X, SHAPE_F1F2>(M.lx, M.vx_alt, s_args, cf, smem, i + 1);
+        }
         __syncthreads();
         if (threadIdx.x == 0 && item != p.hold_item) {
-            __threadfence();
-            atomicAdd(p.done + m, 1u);
+            // release at GPU scope: the CTA's stores (ordered before this thread by the
+            // barrier) are visible to whoever acquires the new count
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p.done + m), "r"(1u) : "memory");
         }
     }
 }
 
-template <int LOGN> void geo_axis(int axis, int lines, int* items, int* smem) {
+template <int LOGN, int AXIS, int VAR> void geo_v(int lines, int* ctas) {
+    using G = Geo<LOGN, AXIS, VAR>;
+    const int blocks = ((lines + G::Cf::BATCH - 1) / G::Cf::BATCH) * G::Cf::NPAIRS;
+    *ctas = (blocks + G::K - 1) / G::K;
+}
+template <int LOGN> void geo_axis(int axis, int alt, int lines, int* ctas) {
     if (axis == AXIS_X) {
-        using G = Geo<LOGN, AXIS_X>;
-        const int blocks = ((lines + G::Cf::BATCH - 1) / G::Cf::BATCH) * G::Cf::NPAIRS;
-        *items = (blocks + G::K - 1) / G::K;
-        *smem = G::SMEM;
+        if (alt) geo_v<LOGN, AXIS_X, kVX1>(lines, ctas); else geo_v<LOGN, AXIS_X, kVX0>(lines, ctas);
     } else {
-        using G = Geo<LOGN, AXIS_Y>;
-        const int blocks = ((lines + G::Cf::BATCH - 1) / G::Cf::BATCH) * G::Cf::NPAIRS;
-        *items = (blocks + G::K - 1) / G::K;
-        *smem = G::SMEM;
+        geo_v<LOGN, AXIS_Y, kVY0>(lines, ctas);
     }
 }
 
 template <int LOGN> int max_smem() {
-    const int a = Geo<LOGN, AXIS_X>::SMEM, b = Geo<LOGN, AXIS_Y>::SMEM;
-    return a > b ? a : b;
+    const int s[3] = {Geo<LOGN, AXIS_X, kVX0>::SMEM, Geo<LOGN, AXIS_X, kVX1>::SMEM,
+                      Geo<LOGN, AXIS_Y, kVY0>::SMEM};
+    int m = 0;
+    for (int v : s) m = v > m ? v : m;
+    return m;
 }
 
 }  // namespace
 
 bool persist_supported(int logn) { return logn >= kMinLog && logn <= kMaxLog; }
 
-int persist_items(int axis, int logn, int lines) {
-    int items = 0, smem = 0;
+int persist_ctas(int axis, int alt, int logn, int lines) {
+    int items = 0;
     switch (logn) {
-        case 4: geo_axis<4>(axis, lines, &items, &smem); break;
-        case 5: geo_axis<5>(axis, lines, &items, &smem); break;
-        case 6: geo_axis<6>(axis, lines, &items, &smem); break;
-        case 7: geo_axis<7>(axis, lines, &items, &smem); break;
-        case 8: geo_axis<8>(axis, lines, &items, &smem); break;
-        case 9: geo_axis<9>(axis, lines, &items, &smem); break;
+        case 4: geo_axis<4>(axis, alt, lines, &items); break;
+        case 5: geo_axis<5>(axis, alt, lines, &items); break;
+        case 6: geo_axis<6>(axis, alt, lines, &items); break;
+        case 7: geo_axis<7>(axis, alt, lines, &items); break;
+        case 8: geo_axis<8>(axis, alt, lines, &items); break;
+        case 9: geo_axis<9>(axis, alt, lines, &items); break;
         default: return -1;
     }
     return items;
 }
 
-void persist_variants(int* vx, int* vy) { *vx = kVX; *vy = kVY; }
+int persist_variant_alt(int axis, int variant) {
+    if (axis == AXIS_X) return variant == kVX1 ? 1 : 0;
+    return 0;
+}
+
+void persist_variants(int axis, int* v0, int* v1) {
+    *v0 = axis == AXIS_X ? kVX0 : kVY0;
+    *v1 = axis == AXIS_X ? kVX1 : kVY0;
+}
 
 cudaError_t launch_persist(const PersistPlan& p, cudaStream_t s) {
     static int smem = 0, grid = 0;

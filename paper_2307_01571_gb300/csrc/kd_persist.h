@@ -17,7 +17,10 @@ namespace kd {
 struct alignas(16) PersistMember {
     SweepArgs y, x, xc;
     int lx, ly;
-    int iy, ix;
+    int iy, ix;      // work items per y / x sweep
+    int cy, cx;      // CTA-fulls of blocks per y / x sweep
+    int gy, gx;      // CTA-fulls per work item (the last item may hold fewer)
+    int vy_alt, vx_alt;   // 1: the axis runs the second of the kernel's two launch variants
     int* status;
 };
 static_assert(sizeof(SweepArgs) % 16 == 0, "SweepArgs is copied in 16-byte words");
@@ -41,10 +44,14 @@ struct PersistPlan {
 
 // Axes of 2^logn points the persistent kernel holds (16 ... 512).
 bool persist_supported(int logn);
-// Work items of one sweep over `lines` lines of 2^logn points (axis AXIS_X or AXIS_Y).
-int persist_items(int axis, int logn, int lines);
-// Launch variants the persistent kernel runs (x, y).
-void persist_variants(int* vx, int* vy);
+// CTA-fulls of blocks of one sweep over `lines` lines of 2^logn points (axis AXIS_X or
+// AXIS_Y, launch variant alt 0/1 of the axis); a work item runs one or more of them.
+int persist_ctas(int axis, int alt, int logn, int lines);
+// The persistent kernel holds two launch variants per axis (v0 the default, v1 the other);
+// persist_variant_alt gives 1 for a simulation's variant that is v1, else 0 (the member
+// then runs v0).
+void persist_variants(int axis, int* v0, int* v1);
+int persist_variant_alt(int axis, int variant);
 cudaError_t launch_persist(const PersistPlan& p, cudaStream_t s);
 
 }  // namespace kd
