@@ -269,6 +269,13 @@ int kd_mlp_gradients(kd_mlp* net, const float* x, const float* targets, int32_t 
                      float* loss, float* grads, int32_t where, void* cuda_stream);
 int kd_mlp_train_step(kd_mlp* net, const float* x, const float* targets, int32_t batch,
                       float lr, float* loss_dev, void* cuda_stream);
+/* The same training step on a minibatch selected on the device: rows idx[0 .. batch) of
+ * x_all [n_all][widths[0]] and targets_all [n_all][widths[nlayers]] (device pointers;
+ * idx device int32, indices outside [0, n_all) select rows of zeros) are gathered by the
+ * library's own kernel into its staging buffers. */
+int kd_mlp_train_step_gather(kd_mlp* net, const float* x_all, const float* targets_all,
+                             int64_t n_all, const int32_t* idx, int32_t batch, float lr,
+                             float* loss_dev, void* cuda_stream);
 void kd_mlp_destroy(kd_mlp* net);
 
 /* Benchmark hook: enqueues `reps` back-to-back launches of one fused sweep on the

@@ -31,6 +31,8 @@ struct kd_mlp {
     float* dbuf0 = nullptr;          // gradient ping-pong buffers [cap][max width]
     float* dbuf1 = nullptr;
     float* lossbuf = nullptr;        // [cap * w[L]] squared errors, then partials
+    float* gx = nullptr;             // gathered minibatch inputs [cap][w[0]]
+    float* gt = nullptr;             // gathered minibatch targets [cap][w[L]]
 };
 
 namespace {
@@ -134,6 +136,17 @@ __global__ void k_sum(const float* x, long n, float scale, float* out) {
     if (threadIdx.x == 0) out[0] = (float)(red[0] * scale);
 }
 
+// dst[i][:] = src[idx[i]][:] for i < n (rows of `width` floats); an index outside
+// [0, nsrc) gives a row of zeros
+__global__ void k_gather_rows(const float* src, int width, long nsrc, const int32_t* idx, int n, float* dst) {
+    const long total = (long)n * width;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / width), j = (int)(e % width);
+        const long r = idx[i];
+        dst[e] = (r >= 0 && r < nsrc) ? src[r * width + j] : 0.0f;
+    }
+}
+
 __global__ void k_adam(float* p, const float* g, float* m1, float* m2, long n, float lr, float b1,
                        float b2, float eps, float c1, float c2) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -166,6 +179,9 @@ int ensure_cap(kd_mlp* n, int batch) {
     cudaFree(n->dbuf0);
     cudaFree(n->dbuf1);
     cudaFree(n->lossbuf);
+    cudaFree(n->gx);
+    cudaFree(n->gt);
+    n->gx = n->gt = nullptr;   // gathered-batch buffers, re-made at the new capacity
     n->z.assign(n->L, nullptr);
     n->a.assign(n->L + 1, nullptr);
     for (int l = 0; l < n->L; ++l) {
@@ -275,6 +291,8 @@ void kd_mlp_destroy(kd_mlp* n) {
     cudaFree(n->dbuf0);
     cudaFree(n->dbuf1);
     cudaFree(n->lossbuf);
+    cudaFree(n->gx);
+    cudaFree(n->gt);
     cudaFree(n->param);
     cudaFree(n->grad);
     cudaFree(n->m1);
@@ -357,6 +375,25 @@ int kd_mlp_gradients(kd_mlp* n, const float* x, const float* t, int32_t batch, f
     cudaFree(tmp_x);
     cudaFree(tmp_t);
     return rc;
+}
+
+int kd_mlp_train_step_gather(kd_mlp* n, const float* x_all, const float* t_all, int64_t n_all,
+                             const int32_t* idx, int32_t batch, float lr, float* loss_dev, void* cuda_stream) {
+    if (!n || !x_all || !t_all || !idx || n_all <= 0 || batch <= 0 || !(lr > 0))
+        return err(KD_ERR_ARG, "kd_mlp_train_step_gather: bad argument");
+    MLP_CUDA(cudaSetDevice(n->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int rc = ensure_cap(n, batch);
+    if (rc) return rc;
+    if (!n->gx) {
+        MLP_CUDA(cudaMalloc(&n->gx, (size_t)n->cap * n->w[0] * sizeof(float)));
+        MLP_CUDA(cudaMalloc(&n->gt, (size_t)n->cap * n->w[n->L] * sizeof(float)));
+    }
+    const int win = n->w[0], wout = n->w[n->L];
+    k_gather_rows<<<(batch * win + 255) / 256, 256, 0, s>>>(x_all, win, (long)n_all, idx, batch, n->gx);
+    k_gather_rows<<<(batch * wout + 255) / 256, 256, 0, s>>>(t_all, wout, (long)n_all, idx, batch, n->gt);
+    MLP_CUDA(cudaGetLastError());
+    return kd_mlp_train_step(n, n->gx, n->gt, batch, lr, loss_dev, cuda_stream);
 }
 
 int kd_mlp_train_step(kd_mlp* n, const float* x, const float* t, int32_t batch, float lr,

@@ -126,6 +126,7 @@ _SIGS = {
     "kd_mlp_forward": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.c_int32, _vp]),
     "kd_mlp_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, _vp, C.c_int32, _vp]),
     "kd_mlp_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_float, _vp, _vp]),
+    "kd_mlp_train_step_gather": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, C.c_int32, C.c_float, _vp, _vp]),
     "kd_mlp_destroy": (None, [_vp]),
     "kd_destroy": (None, [_vp]),
     "kd_last_error": (C.c_char_p, []),
@@ -430,3 +431,10 @@ class MLP:
         """Device pointers (ints, e.g. torch data_ptr())."""
         _check(kd_mlp_train_step(self._h, _vp(x_dev), _vp(t_dev), batch, lr,
                                  _vp(loss_dev) if loss_dev else None, _vp(stream) if stream else None))
+
+    def train_step_gather(self, x_all_dev, t_all_dev, n_all: int, idx_dev, batch: int, lr: float,
+                          loss_dev=None, stream=None):
+        """Training step on rows idx of the device arrays (gathered by the library)."""
+        _check(kd_mlp_train_step_gather(self._h, _vp(x_all_dev), _vp(t_all_dev), n_all, _vp(idx_dev),
+                                        batch, lr, _vp(loss_dev) if loss_dev else None,
+                                        _vp(stream) if stream else None))

@@ -89,3 +89,34 @@ def test_training_reduces_loss(kd):
     l1, _ = net.gradients(x, t)
     assert l1 < 0.02 * l0, (l0, l1)
     net.close()
+
+
+def test_gathered_minibatch_step_equals_plain_step(kd):
+    """kd_mlp_train_step_gather selects the minibatch rows with the library's own gather
+    kernel; the update equals kd_mlp_train_step on the same rows gathered on the host, bit
+    for bit, and an index outside the sample range selects a row of zeros."""
+    import torch
+    x, t = _data(300, 9)
+    p0 = mlp.init_params(WIDTHS, 4)
+    rng = np.random.default_rng(1)
+    steps = [rng.integers(0, 300, 64).astype(np.int32) for _ in range(4)]
+    steps[-1][5] = 300                      # outside [0, n): a zero row
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    a = kd.MLP(WIDTHS)
+    a.set_params(p0)
+    for idx in steps:
+        idev = torch.from_numpy(idx).cuda()
+        a.train_step_gather(xd.data_ptr(), td.data_ptr(), 300, idev.data_ptr(), 64, 1e-3)
+        torch.cuda.synchronize()
+    b = kd.MLP(WIDTHS)
+    b.set_params(p0)
+    for idx in steps:
+        ok = idx < 300
+        xb = np.where(ok[:, None], x[np.minimum(idx, 299)], 0.0).astype(np.float32)
+        tb = np.where(ok[:, None], t[np.minimum(idx, 299)], 0.0).astype(np.float32)
+        xbd, tbd = torch.from_numpy(xb).cuda(), torch.from_numpy(tb).cuda()
+        b.train_step(xbd.data_ptr(), tbd.data_ptr(), 64, 1e-3)
+        torch.cuda.synchronize()
+    assert np.array_equal(a.get_params(), b.get_params())
+    a.close()
+    b.close()
