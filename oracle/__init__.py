@@ -22,21 +22,35 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kd_oracle.c")
 _HDR = os.path.join(_HERE, "kd_oracle.h")
 _LIB = os.path.join(_HERE, "libkd_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "libkd_oracle_omp.so")   # timing variant: rows/columns on threads
 _lock = threading.Lock()
 _lib = None
+_use_omp = False
 
 
-def build(force: bool = False) -> str:
-    """Compile ``libkd_oracle.so`` beside the source (FP64, no fast-math, no FMA contraction)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile ``libkd_oracle.so`` beside the source (FP64, no fast-math, no FMA contraction);
+    with openmp=True the OpenMP timing variant ``libkd_oracle_omp.so`` (same source, the
+    independent rows, columns and grid points on several threads, identical results)."""
+    out = _LIB_OMP if openmp else _LIB
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           *(["-fopenmp"] if openmp else []), "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, out)
+    return out
+
+
+def use_openmp(on: bool) -> None:
+    """Route the calls below to the OpenMP timing variant (on) or the plain build (off)."""
+    global _lib, _use_omp
+    with _lock:
+        if on != _use_omp:
+            _use_omp = on
+            _lib = None
 
 
 class Units(C.Structure):
@@ -82,8 +96,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB)
+            L = C.CDLL(build(openmp=_use_omp))
             sig = {
                 "or_fft1d": [_P, C.c_int32, C.c_int32],
                 "or_fft2d": [_P, C.c_int32, C.c_int32, C.c_int32],

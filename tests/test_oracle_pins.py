@@ -554,3 +554,19 @@ def test_study_definitions():
     # the slope fit recovers an exact power law
     x = np.array([1.0, 2.0, 5.0, 10.0])
     assert abs(studies.fit_slope(x, 3.0 * x ** 2) - 2.0) < 1e-12
+
+
+def test_openmp_timing_variant_equals_plain_oracle():
+    """The OpenMP build (rows, columns and grid points on threads; the timing variant of
+    the CPU baseline) computes exactly what the plain build computes."""
+    wl = W.small(64, 32, W.GAUSS, units=NAT, a0=0.3, nsteps=4)
+    u, g, f, pk = wl.units, wl.grid, wl.field, wl.packet
+    psi = W.random_spinor(64, 32, 4)
+    oracle.use_openmp(False)
+    a = oracle.step(u, g, f, psi, 0.0, wl.dt, 4)
+    try:
+        oracle.use_openmp(True)
+        b = oracle.step(u, g, f, psi, 0.0, wl.dt, 4)
+    finally:
+        oracle.use_openmp(False)
+    assert np.array_equal(a, b)
