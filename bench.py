@@ -394,11 +394,20 @@ def surrogate_form(n_runs: int = 4096):
     t_pred = (time.perf_counter() - t0) / (20 * (n_runs - n_tr))
     err = S.heldout_error(pred, Y[n_tr:])
     base = S.heldout_error(np.tile(Y[:n_tr].mean(0), (n_runs - n_tr, 1)), Y[n_tr:])
+    # the same network trained with BF16 tensor-core products
+    from paper_2307_01571_gb300 import kd
+    s16 = S.Surrogate(seed=0, precision=kd.KD_MLP_BF16)
+    t_fit16 = s16.fit(X[:n_tr], Y[:n_tr], steps=4000, batch=256, lr=2e-3)
+    err16 = S.heldout_error(s16.predict(X[n_tr:]), Y[n_tr:])
     return {"runs": n_runs, "train": n_tr, "heldout": n_runs - n_tr,
             "solver_s_per_run_batched": secs / n_runs, "train_s": t_fit,
             "predict_s_per_sample": t_pred, "speedup_vs_solver": secs / n_runs / t_pred,
             "heldout_rms_log10": {k: v["rms"] for k, v in err.items()},
+            "bf16_tensor_core": {"train_s": t_fit16,
+                                 "heldout_rms_log10": {k: v["rms"] for k, v in err16.items()},
+                                 "heldout_max_log10": {k: v["max"] for k, v in err16.items()}},
             "heldout_max_log10": {k: v["max"] for k, v in err.items()},
+            "heldout_worst": S.worst_cases(pred, Y[n_tr:], X[n_tr:], k=3),
             "constant_predictor_rms_log10": {k: v["rms"] for k, v in base.items()}}
 
 
@@ -681,6 +690,18 @@ def main():
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"4 Strang steps of the 1024x512 FP64 run ({dt:.1f} s)",
                                 "host": host_info()}
+        # the same oracle source built with OpenMP (independent rows, columns and points on
+        # every host core; identical results), on the same sample
+        import oracle
+        oracle.use_openmp(True)
+        try:
+            r_omp, dt_omp, _ = oracle_rate(wlc, 32)
+        finally:
+            oracle.use_openmp(False)
+        line["cpu_baseline_openmp"] = {"value": r_omp, "unit": UNIT, "cores": os.cpu_count(),
+                                       "kind": "oracle, OpenMP over rows, columns and grid points",
+                                       "sample": f"32 Strang steps of the 1024x512 FP64 run ({dt_omp:.1f} s)",
+                                       "speedup_over_one_core": r_omp / r}
     if dist:
         dist.barrier()
         dist.destroy_process_group()

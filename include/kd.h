@@ -276,6 +276,15 @@ int kd_mlp_train_step(kd_mlp* net, const float* x, const float* targets, int32_t
 int kd_mlp_train_step_gather(kd_mlp* net, const float* x_all, const float* targets_all,
                              int64_t n_all, const int32_t* idx, int32_t batch, float lr,
                              float* loss_dev, void* cuda_stream);
+/* Arithmetic of the network's matrix products (forward and backward): KD_MLP_FP32 (the
+ * default: FP32 tiled GEMM on the CUDA cores) or KD_MLP_BF16 (operands rounded to BF16,
+ * products on the tcgen05 tensor cores with FP32 accumulation in tensor memory; the
+ * epilogues, GELU, loss and Adam stay FP32).  Each BF16 product waits for the tensor cores
+ * with a bounded wait; if one gives up, the next synchronising call (kd_mlp_forward to
+ * host memory, kd_mlp_gradients, kd_mlp_get_params) returns KD_ERR_TIMEOUT. */
+#define KD_MLP_FP32 0
+#define KD_MLP_BF16 1
+int kd_mlp_set_precision(kd_mlp* net, int32_t precision);
 void kd_mlp_destroy(kd_mlp* net);
 
 /* Benchmark hook: enqueues `reps` back-to-back launches of one fused sweep on the

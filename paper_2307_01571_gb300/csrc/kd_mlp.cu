@@ -1,9 +1,12 @@
 // kd_mlp.cu -- the surrogate network: a fully connected MLP with exact-erf GELU hidden
 // layers, trained on the batched solver's outputs (seeded parameter draws -> diffraction
-// and spin-flip populations).  Hand-written FP32 kernels: tiled GEMM with fused bias /
-// GELU epilogue, the GELU derivative, fixed-order column sums, MSE loss and Adam.
-// Every reduction runs in a fixed order, so training is bitwise reproducible.
+// and spin-flip populations).  Hand-written kernels: tiled GEMM with fused bias / GELU
+// epilogue (FP32 on the CUDA cores, or BF16 operands on the tcgen05 tensor cores with FP32
+// accumulation in tensor memory), the GELU derivative, fixed-order column sums, MSE loss
+// and Adam.  Every reduction runs in a fixed order, so training is bitwise reproducible.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 #include <math.h>
 
 #include <vector>
@@ -33,6 +36,8 @@ struct kd_mlp {
     float* lossbuf = nullptr;        // [cap * w[L]] squared errors, then partials
     float* gx = nullptr;             // gathered minibatch inputs [cap][w[0]]
     float* gt = nullptr;             // gathered minibatch targets [cap][w[L]]
+    int prec = 0;                    // KD_MLP_FP32 or KD_MLP_BF16 (tensor-core GEMMs)
+    int* status = nullptr;           // set when a tensor-core GEMM's bounded wait gave up
 };
 
 namespace {
@@ -99,6 +104,169 @@ __global__ void __launch_bounds__(256) k_gemm(const float* A, long sam, long sak
 }
 
 // dZ = dY * GELU'(Z), elementwise
+// ------------------------------------------------------ BF16 tensor-core GEMM -----
+// The same product and epilogues as k_gemm with BF16 operands (rounded to nearest from
+// the FP32 inputs while staging) on the 5th-generation tensor cores, FP32 accumulation in
+// tensor memory.  One CTA of 128 threads computes a 128 x 64 tile of C: thread r owns row
+// m0 + r, which is TMEM lane r.  Per 64-deep k slab the threads stage A (128 x 64) and B
+// (64 x 64, n by k) in shared memory in the no-swizzle K-major canonical layout (8-row x
+// 16-byte core matrices: LBO = 128 B between core matrices along k, SBO = 1024 B between
+// 8-row groups), thread 0 issues four tcgen05.mma.kind::f16 (M 128, N 64, K 16; A and B
+// both BF16) and commits them to an mbarrier; all threads wait for it (bounded) before the
+// next slab overwrites the operands.  A wait that runs out sets *status and the CTA skips
+// the rest (the host reports KD_ERR_TIMEOUT).
+namespace tcg {
+constexpr uint32_t LBO = 128, SBO = 1024;
+constexpr uint32_t A_BYTES = 16 * SBO, B_BYTES = 8 * SBO;
+constexpr uint32_t OFF_A = 0, OFF_B = A_BYTES, OFF_BAR = A_BYTES + B_BYTES, OFF_SLOT = OFF_BAR + 8;
+constexpr uint32_t SMEM = OFF_SLOT + 8;
+constexpr uint32_t TMEM_COLS = 64;
+// instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1), B BF16
+// (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+constexpr long long WAIT_LIMIT = 1ll << 20;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const uint32_t a = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return a | (b << 16);
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+}  // namespace tcg
+
+__global__ void __launch_bounds__(128) k_gemm_bf16(const float* A, long sam, long sak, const float* B,
+                                                   long sbk, long sbn, float* C, float* Y, const float* bias,
+                                                   int M, int N, int K, int epi, int* status) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int t = threadIdx.x, w = t >> 5;
+    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 64;
+    const uint32_t s0 = tcg::su32(sm), bar = s0 + tcg::OFF_BAR;
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(s0 + tcg::OFF_SLOT), "r"(tcg::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *reinterpret_cast<const uint32_t*>(sm + tcg::OFF_SLOT);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int m = m0 + t;
+    for (int k0 = 0; k0 < K && ok; k0 += 64) {
+        // A row m (= TMEM lane t): 8 core chunks of 8 k
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = k0 + 8 * c + e;
+                v[e] = (m < M && k < K) ? A[m * sam + k * sak] : 0.0f;
+            }
+            const uint32_t o = (uint32_t)(t >> 3) * tcg::SBO + (uint32_t)c * tcg::LBO + (uint32_t)(t & 7) * 16;
+            *reinterpret_cast<uint4*>(sm + tcg::OFF_A + o) =
+                make_uint4(tcg::pack_bf16(v[0], v[1]), tcg::pack_bf16(v[2], v[3]), tcg::pack_bf16(v[4], v[5]),
+                           tcg::pack_bf16(v[6], v[7]));
+        }
+        // B row n (= output column n0 + nn), k half hh: 4 core chunks of 8 k
+        {
+            const int nn = t & 63, hh = t >> 6, n = n0 + nn;
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {
+                const int c = 4 * hh + c4;
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int k = k0 + 8 * c + e;
+                    v[e] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0f;
+                }
+                const uint32_t o = (uint32_t)(nn >> 3) * tcg::SBO + (uint32_t)c * tcg::LBO + (uint32_t)(nn & 7) * 16;
+                *reinterpret_cast<uint4*>(sm + tcg::OFF_B + o) =
+                    make_uint4(tcg::pack_bf16(v[0], v[1]), tcg::pack_bf16(v[2], v[3]), tcg::pack_bf16(v[4], v[5]),
+                               tcg::pack_bf16(v[6], v[7]));
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (t == 0) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t da = tcg::sdesc(s0 + tcg::OFF_A + (uint32_t)ks * 2 * tcg::LBO, tcg::LBO, tcg::SBO);
+                const uint64_t db = tcg::sdesc(s0 + tcg::OFF_B + (uint32_t)ks * 2 * tcg::LBO, tcg::LBO, tcg::SBO);
+                const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                             :: "r"(tmem), "l"(da), "l"(db), "r"(tcg::IDESC), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(bar) : "memory");
+        }
+        const bool got = tcg::mbar_wait(bar, phase);
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        ok = __syncthreads_and(got) != 0;
+    }
+    if (ok && K > 0) {
+        // row m's 64 columns from TMEM lane t: four 16-column loads
+        const uint32_t trow = tmem + ((uint32_t)((w & 3) * 32) << 16);
+        uint32_t r[64];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[16 * j + 0]), "=r"(r[16 * j + 1]), "=r"(r[16 * j + 2]), "=r"(r[16 * j + 3]),
+                           "=r"(r[16 * j + 4]), "=r"(r[16 * j + 5]), "=r"(r[16 * j + 6]), "=r"(r[16 * j + 7]),
+                           "=r"(r[16 * j + 8]), "=r"(r[16 * j + 9]), "=r"(r[16 * j + 10]), "=r"(r[16 * j + 11]),
+                           "=r"(r[16 * j + 12]), "=r"(r[16 * j + 13]), "=r"(r[16 * j + 14]), "=r"(r[16 * j + 15])
+                         : "r"(trow + 16 * j));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m < M) {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int n = n0 + j;
+                if (n >= N) break;
+                float c = __uint_as_float(r[j]);
+                if (epi >= 1) c += bias[n];
+                if (epi == 2) {
+                    C[(long)m * N + n] = c;
+                    Y[(long)m * N + n] = gelu(c);
+                } else {
+                    C[(long)m * N + n] = c;
+                }
+            }
+        }
+    }
+    if (!ok && t == 0) {
+        atomicOr(status, 1);
+        tcg::mbar_wait(bar, phase ^ 1u);   // products possibly in flight: bounded wait
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (w == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tcg::TMEM_COLS));
+}
+
 __global__ void k_gelu_back(const float* dY, const float* Z, float* dZ, long n) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         dZ[i] = dY[i] * gelu_grad(Z[i]);
@@ -159,11 +327,35 @@ __global__ void k_adam(float* p, const float* g, float* m1, float* m2, long n, f
     }
 }
 
-cudaError_t gemm(const float* A, long sam, long sak, const float* B, long sbk, long sbn, float* C,
-                 float* Y, const float* bias, int M, int N, int K, int epi, cudaStream_t s) {
+cudaError_t gemm(const kd_mlp* net, const float* A, long sam, long sak, const float* B, long sbk, long sbn,
+                 float* C, float* Y, const float* bias, int M, int N, int K, int epi, cudaStream_t s) {
+    if (net->prec == KD_MLP_BF16) {
+        // at least 28 KB of shared memory per CTA: at most 8 CTAs per SM, so their tensor
+        // memory (64 columns each) fits the SM's 512 columns without waiting
+        static bool attr = false;
+        constexpr int smem = tcg::SMEM > 28 * 1024 ? (int)tcg::SMEM : 28 * 1024;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        dim3 grid((N + 63) / 64, (M + 127) / 128);
+        k_gemm_bf16<<<grid, 128, smem, s>>>(A, sam, sak, B, sbk, sbn, C, Y, bias, M, N, K, epi, net->status);
+        return cudaGetLastError();
+    }
     dim3 grid((N + 63) / 64, (M + 63) / 64);
     k_gemm<<<grid, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, C, Y, bias, M, N, K, epi);
     return cudaGetLastError();
+}
+
+// KD_ERR_TIMEOUT (and the flag cleared) when a tensor-core GEMM's bounded wait gave up
+// since the last check; synchronises the device
+int check_status(kd_mlp* n) {
+    int st = 0;
+    MLP_CUDA(cudaMemcpy(&st, n->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!st) return KD_OK;
+    MLP_CUDA(cudaMemset(n->status, 0, sizeof(int)));
+    return err(KD_ERR_TIMEOUT, "kd_mlp: a tensor-core GEMM's wait for its products gave up");
 }
 
 int maxw(const kd_mlp* n) {
@@ -203,7 +395,7 @@ int forward(kd_mlp* n, const float* x, int batch, cudaStream_t s) {
         const int fi = n->w[l], fo = n->w[l + 1];
         const bool last = l == n->L - 1;
         float* out = last ? n->a[l + 1] : n->z[l];
-        MLP_CUDA(gemm(n->a[l], fi, 1, n->param + n->woff[l], 1, fi, out, last ? nullptr : n->a[l + 1],
+        MLP_CUDA(gemm(n, n->a[l], fi, 1, n->param + n->woff[l], 1, fi, out, last ? nullptr : n->a[l + 1],
                       n->param + n->boff[l], batch, fo, fi, last ? 1 : 2, s));
     }
     return KD_OK;
@@ -228,11 +420,11 @@ int backward(kd_mlp* n, const float* t, int batch, cudaStream_t s) {
             MLP_CUDA(cudaGetLastError());
         }
         // dW_l[o][i] = sum_b dZ[b][o] a_l[b][i];  db_l[o] = sum_b dZ[b][o]
-        MLP_CUDA(gemm(dcur, 1, fo, n->a[l], fi, 1, n->grad + n->woff[l], nullptr, nullptr, fo, fi, batch, 0, s));
+        MLP_CUDA(gemm(n, dcur, 1, fo, n->a[l], fi, 1, n->grad + n->woff[l], nullptr, nullptr, fo, fi, batch, 0, s));
         k_colsum<<<(fo + 127) / 128, 128, 0, s>>>(dcur, batch, fo, n->grad + n->boff[l]);
         MLP_CUDA(cudaGetLastError());
         if (l > 0) {  // dA_{l}[b][i] = sum_o dZ[b][o] W_l[o][i]
-            MLP_CUDA(gemm(dcur, fo, 1, n->param + n->woff[l], fi, 1, dnext, nullptr, nullptr, batch, fi, fo, 0, s));
+            MLP_CUDA(gemm(n, dcur, fo, 1, n->param + n->woff[l], fi, 1, dnext, nullptr, nullptr, batch, fi, fo, 0, s));
             float* tmp = dcur;
             dcur = dnext;
             dnext = tmp;
@@ -273,6 +465,8 @@ int kd_mlp_create(const int32_t* widths, int32_t nlayers, kd_mlp** out) {
     if (cudaMalloc(&n->param, off * sizeof(float)) != cudaSuccess || cudaMalloc(&n->grad, off * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&n->m1, off * sizeof(float)) != cudaSuccess || cudaMalloc(&n->m2, off * sizeof(float)) != cudaSuccess)
         return bail(err(KD_ERR_NOMEM, "kd_mlp_create: allocation failed"));
+    if (cudaMalloc(&n->status, sizeof(int)) != cudaSuccess || cudaMemset(n->status, 0, sizeof(int)) != cudaSuccess)
+        return bail(err(KD_ERR_NOMEM, "kd_mlp_create: allocation failed"));
     if (cudaMemset(n->param, 0, off * sizeof(float)) != cudaSuccess || cudaMemset(n->m1, 0, off * sizeof(float)) != cudaSuccess ||
         cudaMemset(n->m2, 0, off * sizeof(float)) != cudaSuccess || cudaMemset(n->grad, 0, off * sizeof(float)) != cudaSuccess)
         return bail(err(KD_ERR_CUDA, "kd_mlp_create: memset failed"));
@@ -293,6 +487,7 @@ void kd_mlp_destroy(kd_mlp* n) {
     cudaFree(n->lossbuf);
     cudaFree(n->gx);
     cudaFree(n->gt);
+    cudaFree(n->status);
     cudaFree(n->param);
     cudaFree(n->grad);
     cudaFree(n->m1);
@@ -324,6 +519,13 @@ int kd_mlp_get_params(kd_mlp* n, float* p, int32_t where) {
     int rc = copy_io(p, n->param, n->nparam * sizeof(float), where, KD_DEVICE, 0);
     if (rc) return rc;
     MLP_CUDA(cudaDeviceSynchronize());
+    return check_status(n);
+}
+
+int kd_mlp_set_precision(kd_mlp* n, int32_t precision) {
+    if (!n || (precision != KD_MLP_FP32 && precision != KD_MLP_BF16))
+        return err(KD_ERR_ARG, "kd_mlp_set_precision: KD_MLP_FP32 or KD_MLP_BF16");
+    n->prec = precision;
     return KD_OK;
 }
 
@@ -343,7 +545,10 @@ int kd_mlp_forward(kd_mlp* n, const float* x, int32_t batch, float* y, int32_t w
     if (rc) return rc;
     rc = copy_io(y, n->a[n->L], sizeof(float) * (size_t)batch * n->w[n->L], where, KD_DEVICE, s);
     if (rc) return rc;
-    if (where == KD_HOST) MLP_CUDA(cudaStreamSynchronize(s));
+    if (where == KD_HOST) {
+        MLP_CUDA(cudaStreamSynchronize(s));
+        return check_status(n);
+    }
     return KD_OK;
 }
 
@@ -371,7 +576,10 @@ int kd_mlp_gradients(kd_mlp* n, const float* x, const float* t, int32_t batch, f
     if (!rc) rc = backward(n, td, batch, s);
     if (!rc && loss) rc = copy_io(loss, n->lossbuf, sizeof(float), where, KD_DEVICE, s);
     if (!rc && grads) rc = copy_io(grads, n->grad, n->nparam * sizeof(float), where, KD_DEVICE, s);
-    if (where == KD_HOST) cudaStreamSynchronize(s);
+    if (where == KD_HOST) {
+        cudaStreamSynchronize(s);
+        if (!rc) rc = check_status(n);
+    }
     cudaFree(tmp_x);
     cudaFree(tmp_t);
     return rc;

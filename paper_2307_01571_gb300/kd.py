@@ -27,6 +27,7 @@ KD_HOST, KD_DEVICE = 0, 1
 KD_SWEEP_VARIANTS, KD_TUNE_FORCE = 4, 1
 KD_FAULT_TC_WAIT, KD_FAULT_PERSIST_HOLD = 1, 2
 KD_BATCH_GRAPH, KD_BATCH_PERSISTENT = 0, 1
+KD_MLP_FP32, KD_MLP_BF16 = 0, 1
 
 
 class KdError(RuntimeError):
@@ -127,6 +128,7 @@ _SIGS = {
     "kd_mlp_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, _vp, C.c_int32, _vp]),
     "kd_mlp_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_float, _vp, _vp]),
     "kd_mlp_train_step_gather": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, C.c_int32, C.c_float, _vp, _vp]),
+    "kd_mlp_set_precision": (C.c_int, [_vp, C.c_int32]),
     "kd_mlp_destroy": (None, [_vp]),
     "kd_destroy": (None, [_vp]),
     "kd_last_error": (C.c_char_p, []),
@@ -400,6 +402,10 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+    def set_precision(self, precision: int):
+        """KD_MLP_FP32 or KD_MLP_BF16 (tensor-core products) -- ``kd_mlp_set_precision``."""
+        _check(kd_mlp_set_precision(self._h, precision))
 
     def set_params(self, p):
         a = np.ascontiguousarray(p, np.float32)

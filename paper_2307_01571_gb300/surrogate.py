@@ -114,9 +114,11 @@ def he_init(widths, seed: int) -> np.ndarray:
 class Surrogate:
     """MLP surrogate with the solver as fallback outside the trained parameter box."""
 
-    def __init__(self, seed: int = 0, widths=WIDTHS):
+    def __init__(self, seed: int = 0, widths=WIDTHS, precision: int = kd.KD_MLP_FP32):
+        """precision: kd.KD_MLP_FP32 (CUDA-core GEMMs) or kd.KD_MLP_BF16 (tensor cores)."""
         self.widths = list(widths)
         self.net = kd.MLP(self.widths)
+        self.net.set_precision(precision)
         self.net.set_params(he_init(self.widths, seed))
         self.xs = self.ys = None
 
@@ -166,9 +168,25 @@ class Surrogate:
         return out, ~ok
 
 
+TARGET_NAMES = ["log10_P_in", "log10_P_bragg", "log10_P_bragg_same_spin", "log10_P_bragg_flip"]
+PARAM_NAMES = ["w0_lambda", "log10_a0", "env_steps", "px0_hk", "spin"]
+
+
 def heldout_error(pred, truth) -> dict:
     """Errors in log10 space per target (RMS and max |error|, decades)."""
     d = np.asarray(pred) - np.asarray(truth)
-    names = ["log10_P_in", "log10_P_bragg", "log10_P_bragg_same_spin", "log10_P_bragg_flip"]
     return {n: {"rms": float(np.sqrt(np.mean(d[:, j] ** 2))), "max": float(np.max(np.abs(d[:, j])))}
-            for j, n in enumerate(names)}
+            for j, n in enumerate(TARGET_NAMES)}
+
+
+def worst_cases(pred, truth, params, k: int = 3) -> dict:
+    """Per target, the k held-out rows of largest |error|: parameters, truth and prediction
+    (log10), and the row's other targets (to see where in the physics the error sits)."""
+    pred, truth, params = np.asarray(pred), np.asarray(truth), np.asarray(params)
+    out = {}
+    for j, n in enumerate(TARGET_NAMES):
+        idx = np.argsort(-np.abs(pred[:, j] - truth[:, j]))[:k]
+        out[n] = [{"params": dict(zip(PARAM_NAMES, map(float, params[i]))),
+                   "truth": [float(v) for v in truth[i]], "pred": [float(v) for v in pred[i]]}
+                  for i in idx]
+    return out

@@ -120,3 +120,52 @@ def test_gathered_minibatch_step_equals_plain_step(kd):
     assert np.array_equal(a.get_params(), b.get_params())
     a.close()
     b.close()
+
+
+# BF16 products on the tensor cores: every operand rounded to 8 significand bits (relative
+# 2^-9), sums over K in FP32; outputs within a few 2^-9 of the FP64 oracle's scale
+BF16_TOL = 2e-2
+
+
+@pytest.mark.parametrize("batch", [1, 37, 300])
+def test_bf16_tensor_core_forward_and_gradients_match_oracle(kd, batch):
+    net = kd.MLP(WIDTHS)
+    net.set_precision(kd.KD_MLP_BF16)
+    p = mlp.init_params(WIDTHS, 7)
+    net.set_params(p)
+    x, t = _data(batch, batch)
+    y = net.forward(x)
+    yr, _, _ = mlp.forward(p.astype(np.float64), WIDTHS, x.astype(np.float64))
+    assert np.max(np.abs(y - yr)) <= BF16_TOL * max(1.0, np.max(np.abs(yr)))
+    loss, g = net.gradients(x, t)
+    lr_, gr = mlp.loss_and_grad(p.astype(np.float64), WIDTHS, x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - lr_) <= BF16_TOL * max(1.0, lr_)
+    assert np.max(np.abs(g - gr)) <= BF16_TOL * np.max(np.abs(gr))
+    # the BF16 result is not the FP32 one (the tensor-core path really ran)
+    net32 = kd.MLP(WIDTHS)
+    net32.set_params(p)
+    assert not np.array_equal(net32.forward(x), y)
+    net.close()
+    net32.close()
+
+
+def test_bf16_training_reduces_loss_and_is_deterministic(kd):
+    import torch
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, (512, 5)).astype(np.float32)
+    t = np.stack([np.sin(2 * x[:, 0]) * x[:, 1], x[:, 2] ** 2, np.cos(x[:, 3] + x[:, 4]), x.sum(1) / 5], 1).astype(np.float32)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    finals = []
+    for _ in range(2):
+        net = kd.MLP(WIDTHS)
+        net.set_precision(kd.KD_MLP_BF16)
+        net.set_params(mlp.init_params(WIDTHS, 2))
+        l0, _ = net.gradients(x, t)
+        for _ in range(400):
+            net.train_step(xd.data_ptr(), td.data_ptr(), 512, 2e-3)
+        torch.cuda.synchronize()
+        l1, _ = net.gradients(x, t)
+        assert l1 < 0.1 * l0, (l0, l1)
+        finals.append(net.get_params())
+        net.close()
+    assert np.array_equal(finals[0], finals[1])
