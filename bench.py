@@ -253,6 +253,8 @@ def batched_form(kd, stream, K, barrier, dist):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / K
+    # every member after warm-up + K runs in the graph form, to check the persistent form
+    psi_graph = [s_.get_spinor() for s_ in sims]
     # the persistent form: one kernel per chunk with a device work queue (fixed variants)
     for s_, w in zip(sims, members):
         s_.init_packet(w.packet)
@@ -269,6 +271,10 @@ def batched_form(kd, stream, K, barrier, dist):
         e1.record(stream)
         e1.synchronize()
         ms_p = e0.elapsed_time(e1) / K
+    # same runs, same step count: the two forms differ only in launch variants (rounding)
+    diff_p = max(float(np.max(np.abs(s_.get_spinor() - g)) / np.max(np.abs(g)))
+                 for s_, g in zip(sims, psi_graph))
+    del psi_graph
     for s_, w in zip(sims, members):                           # the same runs one by one,
         s_.autotune(w.dt)                                      # on the variants tuned alone
         s_.step(w.dt, w.nsteps, obs_every=100)
@@ -291,7 +297,8 @@ def batched_form(kd, stream, K, barrier, dist):
                 "persistent": {"value": pts / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p,
                                "form": "one persistent kernel per 100-step chunk, device work queue of "
                                        "(step, sweep, member, block group) items, bounded waits",
-                               "over_graph_branches": ms / ms_p}})
+                               "over_graph_branches": ms / ms_p,
+                               "max_rel_diff_vs_graph_form": diff_p}})
     return res
 
 

@@ -240,11 +240,15 @@ int kd_batch_autotune(kd_batch* batch, const double* dt, int32_t steps, int32_t*
  * KD_ERR_TIMEOUT (the members' states are then not valid evolutions).  The observation and
  * opening-half work at chunk ends runs as graph branches beside it, and the whole chunk is
  * one CUDA-graph launch.  Every member must be KD_FP32 with both axes of 16 ... 512 points
- * (else KD_ERR_UNSUPPORTED_SIZE).  The kernel holds launch variants x 0 and 2 and y 3: a
- * member's x sweep runs its own variant when it is 2 (as kd_autotune picks for small
- * grids), else 0; its y sweep runs 3.  A member advanced this way equals the member
- * advanced alone on those variants, bit for bit.  KD_BATCH_GRAPH (the default) restores the graph-branch form.  The persistent form
- * holds device buffers of its own (descriptors and counters, O(n)).  Synchronises. */
+ * (else KD_ERR_UNSUPPORTED_SIZE).  The kernel holds launch variants x 0 and 2 and y 3 and
+ * 2: a member's x sweep runs its own variant when it is 2 (as kd_autotune picks for small
+ * grids), else 0; its y sweep runs 2 when that is its variant and the y axis has at most
+ * 256 points, else 3; entering the persistent form (and every persistent step) sets each
+ * member's variants to those it runs (kd_get_sweep_variants reports them), so that its
+ * sweeps outside the kernel run them too.  A member advanced this way equals the member
+ * advanced alone on those variants, bit for bit.  KD_BATCH_GRAPH (the default) restores the graph-branch
+ * form.  The persistent form holds device buffers of its own (descriptors and counters,
+ * O(n)).  Synchronises. */
 #define KD_BATCH_GRAPH 0
 #define KD_BATCH_PERSISTENT 1
 int kd_batch_set_mode(kd_batch* batch, int32_t mode);

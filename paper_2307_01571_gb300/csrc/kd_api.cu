@@ -1770,6 +1770,24 @@ struct kd_batch {
 
 namespace {
 
+// Persistent form: each member's launch variants become the ones the kernel runs for it
+// (its own where the kernel holds them, else the axis default), so that the sweep
+// arguments (the twiddle tables follow the variant's radix schedule) and the sweeps that
+// run outside the kernel (half sweeps at chunk ends, read-outs) use those same variants.
+void persist_map_variants(kd_batch* b) {
+    for (kd_sim* s : b->sims)
+        for (int ax = 0; ax < 2; ++ax) {
+            const int logn = ax == AXIS_X ? s->lx : s->ly;
+            int v0, v1;
+            persist_variants(ax, logn, &v0, &v1);
+            const int ran = persist_variant_alt(ax, s->var[ax], logn) ? v1 : v0;
+            if (s->var[ax] != ran) {
+                s->var[ax] = ran;
+                clear_graphs(s);
+            }
+        }
+}
+
 // Persistent form: uploads this call's member descriptors and the work items' prefix
 // sums, clears the abort flag, and finds the item whose completion the test hook withholds
 // (the first y item of the first held member in the call's first chunk).
@@ -1789,8 +1807,8 @@ int persist_upload(kd_batch* b, const std::vector<StepPlan>& plans, bool* hold) 
         // the member's own launch variants where the kernel holds them, else its defaults;
         // the same number of CTA-fulls per work item for every member (uneven groups let
         // the large members' items set the pace of every sweep)
-        m.vx_alt = persist_variant_alt(AXIS_X, s->var[AXIS_X]);
-        m.vy_alt = persist_variant_alt(AXIS_Y, s->var[AXIS_Y]);
+        m.vx_alt = persist_variant_alt(AXIS_X, s->var[AXIS_X], s->lx);
+        m.vy_alt = persist_variant_alt(AXIS_Y, s->var[AXIS_Y], s->ly);
         m.cy = persist_ctas(AXIS_Y, m.vy_alt, s->ly, s->g.nx);
         m.cx = persist_ctas(AXIS_X, m.vx_alt, s->lx, s->g.ny);
         m.gy = m.gx = b->persist_group;
@@ -1929,6 +1947,7 @@ int kd_batch_step(kd_batch* b, const double* dt, int64_t nsteps, int64_t obs_eve
     KD_CUDA(cudaSetDevice(b->device));
     if (n_obs) *n_obs = 0;
     const size_t n = b->sims.size();
+    if (b->persistent) persist_map_variants(b);
     std::vector<StepPlan> plans(n);
     for (size_t i = 0; i < n; ++i) {
         int rc = prepare_step(b->sims[i], dt[i], nsteps, obs_every,
@@ -2046,6 +2065,7 @@ int kd_batch_set_mode(kd_batch* b, int32_t mode) {
     }
     KD_CUDA(cudaStreamSynchronize(b->stream));
     b->persistent = mode == KD_BATCH_PERSISTENT;
+    if (b->persistent) persist_map_variants(b);
     clear_batch_graphs(b);
     return KD_OK;
 }
@@ -2129,9 +2149,10 @@ int kd_batch_autotune(kd_batch* b, const double* dt, int32_t steps, int32_t* var
             float best_ms = base;
             for (int v = 0; v < KD_SWEEP_VARIANTS && !rc; ++v) {
                 if (v == cur) continue;
-                if (b->persistent) {   // the persistent kernel holds x variants 0 and 2 only
+                if (b->persistent) {   // the variants the persistent kernel holds
                     int v0, v1;
-                    persist_variants(ax, &v0, &v1);
+                    const kd_sim* s0 = b->sims[kv.second[0]];
+                    persist_variants(ax, ax == AXIS_X ? s0->lx : s0->ly, &v0, &v1);
                     if (v != v0 && v != v1) continue;
                 }
                 for (size_t i : kv.second) set_var(i, ax, v);

@@ -25,9 +25,10 @@ namespace {
 
 constexpr int kThreads = 256;            // CTA size of the persistent kernel
 // launch variants the kernel holds per axis: x radix-8 (default) and radix-4 Stockham
-// stages; y one variant (the radix-4 y variant needs 512-thread CTAs at 512 points)
-constexpr int kVX0 = 0, kVX1 = 2, kVY0 = 3;
-constexpr int kMinLog = 4, kMaxLog = 9;
+// stages; y the 256-thread radix-8 tiles of one pair (default) and the radix-4 tiles of
+// both pairs, the latter up to 256 points (at 512 points it needs 512-thread CTAs)
+constexpr int kVX0 = 0, kVX1 = 2, kVY0 = 3, kVY1 = 2;
+constexpr int kMinLog = 4, kMaxLog = 9, kMaxLogVY1 = 8;
 
 static_assert(sizeof(SweepArgs) % sizeof(int4) == 0, "SweepArgs copies as int4");
 
@@ -62,6 +63,18 @@ __device__ __forceinline__ void run_logn_v(int logn, const SweepArgs& a, int g, 
     }
 }
 
+// the second y variant, held up to kMaxLogVY1 (members of longer y axes never select it)
+template <int SHAPE>
+__device__ __forceinline__ void run_logn_y1(int logn, const SweepArgs& a, int g, unsigned char* smem, int nl) {
+    switch (logn) {
+        case 4: run_group<4, AXIS_Y, SHAPE, kVY1>(a, g, smem, nl); break;
+        case 5: run_group<5, AXIS_Y, SHAPE, kVY1>(a, g, smem, nl); break;
+        case 6: run_group<6, AXIS_Y, SHAPE, kVY1>(a, g, smem, nl); break;
+        case 7: run_group<7, AXIS_Y, SHAPE, kVY1>(a, g, smem, nl); break;
+        default: run_group<8, AXIS_Y, SHAPE, kVY1>(a, g, smem, nl); break;
+    }
+}
+
 // alt selects the second variant of the axis
 template <int AXIS, int SHAPE>
 __device__ __forceinline__ void run_logn(int logn, int alt, const SweepArgs& a, int g, unsigned char* smem, int nl) {
@@ -69,8 +82,8 @@ __device__ __forceinline__ void run_logn(int logn, int alt, const SweepArgs& a, 
         if (alt) run_logn_v<AXIS, SHAPE, kVX1>(logn, a, g, smem, nl);
         else run_logn_v<AXIS, SHAPE, kVX0>(logn, a, g, smem, nl);
     } else {
-        (void)alt;   // one y variant
-        run_logn_v<AXIS, SHAPE, kVY0>(logn, a, g, smem, nl);
+        if (alt && logn <= kMaxLogVY1) run_logn_y1<SHAPE>(logn, a, g, smem, nl);
+        else run_logn_v<AXIS, SHAPE, kVY0>(logn, a, g, smem, nl);
     }
 }
 
@@ -173,13 +186,18 @@ template <int LOGN> void geo_axis(int axis, int alt, int lines, int* ctas) {
     if (axis == AXIS_X) {
         if (alt) geo_v<LOGN, AXIS_X, kVX1>(lines, ctas); else geo_v<LOGN, AXIS_X, kVX0>(lines, ctas);
     } else {
+        if constexpr (LOGN <= kMaxLogVY1) {
+            if (alt) { geo_v<LOGN, AXIS_Y, kVY1>(lines, ctas); return; }
+        }
         geo_v<LOGN, AXIS_Y, kVY0>(lines, ctas);
     }
 }
 
 template <int LOGN> int max_smem() {
-    const int s[3] = {Geo<LOGN, AXIS_X, kVX0>::SMEM, Geo<LOGN, AXIS_X, kVX1>::SMEM,
-                      Geo<LOGN, AXIS_Y, kVY0>::SMEM};
+    int y1 = 0;
+    if constexpr (LOGN <= kMaxLogVY1) y1 = Geo<LOGN, AXIS_Y, kVY1>::SMEM;
+    const int s[4] = {Geo<LOGN, AXIS_X, kVX0>::SMEM, Geo<LOGN, AXIS_X, kVX1>::SMEM,
+                      Geo<LOGN, AXIS_Y, kVY0>::SMEM, y1};
     int m = 0;
     for (int v : s) m = v > m ? v : m;
     return m;
@@ -203,14 +221,14 @@ int persist_ctas(int axis, int alt, int logn, int lines) {
     return items;
 }
 
-int persist_variant_alt(int axis, int variant) {
+int persist_variant_alt(int axis, int variant, int logn) {
     if (axis == AXIS_X) return variant == kVX1 ? 1 : 0;
-    return 0;
+    return variant == kVY1 && logn <= kMaxLogVY1 ? 1 : 0;
 }
 
-void persist_variants(int axis, int* v0, int* v1) {
+void persist_variants(int axis, int logn, int* v0, int* v1) {
     *v0 = axis == AXIS_X ? kVX0 : kVY0;
-    *v1 = axis == AXIS_X ? kVX1 : kVY0;
+    *v1 = axis == AXIS_X ? kVX1 : (logn <= kMaxLogVY1 ? kVY1 : kVY0);
 }
 
 cudaError_t launch_persist(const PersistPlan& p, cudaStream_t s) {

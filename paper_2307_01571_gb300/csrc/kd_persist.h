@@ -47,11 +47,11 @@ bool persist_supported(int logn);
 // CTA-fulls of blocks of one sweep over `lines` lines of 2^logn points (axis AXIS_X or
 // AXIS_Y, launch variant alt 0/1 of the axis); a work item runs one or more of them.
 int persist_ctas(int axis, int alt, int logn, int lines);
-// The persistent kernel holds two launch variants per axis (v0 the default, v1 the other);
-// persist_variant_alt gives 1 for a simulation's variant that is v1, else 0 (the member
-// then runs v0).
-void persist_variants(int axis, int* v0, int* v1);
-int persist_variant_alt(int axis, int variant);
+// The persistent kernel holds two launch variants per axis of 2^logn points (v0 the
+// default, v1 the other; v1 = v0 where only one fits its CTA); persist_variant_alt gives 1
+// for a simulation's variant that is v1, else 0 (the member then runs v0).
+void persist_variants(int axis, int logn, int* v0, int* v1);
+int persist_variant_alt(int axis, int variant, int logn);
 cudaError_t launch_persist(const PersistPlan& p, cudaStream_t s);
 
 }  // namespace kd

@@ -113,25 +113,45 @@ def _mixed_members():
             W.small(16, 512, W.NONE, units=W.ATOMIC)]
 
 
-def test_persistent_batch_equals_members_alone(kd):
+def _persist_ran(var, ny):
+    """The launch variants a member with sweep variants `var` runs in the persistent
+    kernel: x 0 or 2; y 3, or 2 on y axes up to 256 points."""
+    vx = 2 if var[0] == 2 else 0
+    vy = 2 if var[1] == 2 and ny <= 256 else 3
+    return (vx, vy)
+
+
+@pytest.mark.parametrize("variants", [None, (2, 2)])
+def test_persistent_batch_equals_members_alone(kd, variants):
     """One persistent kernel per chunk (device work queue, per-member completion counters)
     advances every member exactly as its own sweeps would: bitwise equal to the members
-    run alone on the same launch variants, over chunks with observations and two calls."""
+    run alone on the same launch variants, over chunks with observations and two calls;
+    with the default variants and with the radix-4 alternates of both axes."""
     wls = _mixed_members()
     alone, alone_obs = [], []
     for wl in wls:
         with kd.Sim.from_workload(wl.with_(precision=1)) as sim:
-            sim.sweep_variants = PERSIST_VARIANTS
+            # the packet is built on the variants the member has when it is initialised
+            # (its own), the steps on those the persistent kernel runs for it
+            if variants is not None:
+                sim.sweep_variants = variants
             sim.init_packet(wl.packet)
+            sim.sweep_variants = PERSIST_VARIANTS if variants is None else _persist_ran(variants, wl.grid.ny)
             o1 = sim.step(wl.dt, 45, obs_every=15)
             o2 = sim.step(wl.dt, 30, obs_every=15)
             alone.append(sim.get_spinor())
             alone_obs.append(o1 + o2)
     sims = [kd.Sim.from_workload(wl.with_(precision=1)) for wl in wls]
     for s, wl in zip(sims, wls):
+        if variants is not None:
+            s.sweep_variants = variants
         s.init_packet(wl.packet)
     with kd.Batch(sims) as b:
         b.set_mode(kd.KD_BATCH_PERSISTENT)
+        # the members now report the variants the kernel runs for them
+        for s, wl in zip(sims, wls):
+            assert s.sweep_variants == (PERSIST_VARIANTS if variants is None
+                                        else _persist_ran(variants, wl.grid.ny))
         o1 = b.step([wl.dt for wl in wls], 45, obs_every=15)
         o2 = b.step([wl.dt for wl in wls], 30, obs_every=15)
     for i, s in enumerate(sims):

@@ -16,12 +16,14 @@ from paper_2307_01571_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-# relative error bound over the runs per precision: the FP64 and FP32 bars of the short
-# tests (measured at 2000 steps: 6e-13 and 3.3e-6); the precision form's tensor cores
-# truncate in their FP32 accumulation, so its norm decays by ~7e-7 per step and its error
-# grows with it (measured 1.3e-4 after 200 steps, 1.4e-3 after 2000): stated bound 3e-3
-# the double-word form (3) has FP64's bar
-TOL = {0: 1e-10, 1: 1e-4, 2: 3e-3, 3: 1e-10}
+# relative error bound over the runs per precision: the FP64 and FP32 bars (measured at 2000
+# steps: 6e-13 and 3.3e-6); the double-word form (3) has FP64's bar; the precision form (2)
+# is held to the FP32 bar and misses it: its tensor cores truncate in their FP32
+# accumulation, so its norm decays by ~7e-7 per step and its error grows with it (measured
+# 1.3e-4 after 200 steps, 1.4e-3 after 2000) -- an expected failure
+TOL = {0: 1e-10, 1: 1e-4, 2: 1e-4, 3: 1e-10}
+PRECS = [0, 1, pytest.param(2, marks=pytest.mark.xfail(
+    strict=True, reason="tensor-core FP32 accumulation truncates: error 1.4e-3 after 2000 steps")), 3]
 
 
 def records(name):
@@ -63,7 +65,7 @@ def run_and_compare(kd, wl, rec_set, prec):
     return out
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", PRECS)
 def test_1024x512_full_run(kd, prec):
     rs = records("c2")
     res = run_and_compare(kd, W.c2(), rs, prec)
@@ -72,7 +74,7 @@ def test_1024x512_full_run(kd, prec):
         assert oerr <= TOL[prec], (n, oerr)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", PRECS)
 def test_2048x1024_full_run(kd, prec):
     rs = records("c3")
     res = run_and_compare(kd, W.c3(), rs, prec)

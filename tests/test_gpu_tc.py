@@ -3,8 +3,8 @@
 element on both axes and every field kind (several tiles: 4 lines per work item, many
 items per CTA), at the 1024x512 and 2048x1024 grids, observables through the mixed path
 (tensor-core full sweeps, CUDA-core half sweeps), checkpoints interchangeable with KD_FP32,
-the norm drift the truncating tensor-core accumulation gives (stated bound), and the
-bounded-wait timeout path."""
+the FP32 norm-drift bar as an expected failure (the truncating tensor-core accumulation
+misses it) beside a regression guard, and the bounded-wait timeout path."""
 import math
 
 import numpy as np
@@ -81,18 +81,28 @@ def test_tc_full_size_with_observables(kd, wlf):
         assert abs(obs[-1][k] - v) <= 1e-4 * max(1.0, abs(v)), k
 
 
-def test_tc_norm_drift_bound(kd):
-    """The tensor cores' FP32 accumulation truncates, which biases every product toward
-    zero: the norm of the 1024x512 run decays by ~1e-3 over 2000 steps (FP32 CUDA-core path:
-    random walk below 1e-6).  Stated bound: 3e-3."""
+def _tc_drift(kd):
     wl = W.c2(precision=TC)
     with kd.Sim.from_workload(wl) as sim:
         sim.init_packet(wl.packet)
         n0 = sim.observe()["norm"]
         obs = sim.step(wl.dt, wl.nsteps, obs_every=wl.obs_every)
-    drift = max(abs(o["norm"] - n0) for o in obs)
-    assert drift <= 3e-3, drift
     assert all(math.isfinite(o["pop_diff"]) for o in obs)
+    return max(abs(o["norm"] - n0) for o in obs)
+
+
+@pytest.mark.xfail(strict=True, reason="the tensor cores' FP32 accumulation truncates (bias toward "
+                   "zero); the norm of the 1024x512 run decays by ~1.5e-3 over 2000 steps")
+def test_tc_norm_drift_meets_fp32_bar(kd):
+    """The FP32 bar of norm drift <= 1e-6 over the 2000-step run: the precision form does not
+    meet it (an expected failure; the FP32 CUDA-core form does, test_gpu_long)."""
+    assert _tc_drift(kd) <= 1e-6
+
+
+def test_tc_norm_drift_regression_guard(kd):
+    """Not the bar: guards the measured behaviour of the form (drift 1.5e-3, monotone decay
+    from the truncating accumulation) against getting worse."""
+    assert _tc_drift(kd) <= 3e-3
 
 
 def test_tc_checkpoint_interchangeable_with_fp32(kd):
@@ -172,3 +182,40 @@ def test_tc_injected_wait_fault_lasts_one_batch_step(kd):
         b.step([wl.dt], 2)
     assert np.array_equal(sim.get_spinor(), ref)
     sim.close()
+
+
+def test_tensor_core_fp32_accumulation_rounds_toward_zero(kd):
+    """Why the precision form misses the FP32 bars: the FP32 accumulation of a
+    tcgen05.mma (kind::f16) rounds toward zero.  Sums whose exact value lies between two
+    floats, formed through the library's BF16 tensor-core GEMM (a one-layer network
+    y = W x, W = 1, bias 0, so y is the MMA's sum): 1 + 0.75 ulp comes back as 1 (round to
+    nearest: 1 + 1 ulp), -(1 + 0.75 ulp) as -1, 1 + 1.5 ulp as 1 + 1 ulp (nearest: + 2 ulp),
+    also when the small part arrives in a later 64-deep slab (accumulation in tensor
+    memory).  Every operand is exact in BF16."""
+    u = 2.0 ** -23
+    rows = [[1.0, 0.75 * u], [-1.0, -0.75 * u], [1.0, 1.5 * u], [1.0, 0.25 * u, 0.25 * u, 0.25 * u]]
+    want_rz = [1.0, -1.0, 1.0 + u, 1.0]
+    net = kd.MLP([16, 1])
+    net.set_precision(kd.KD_MLP_BF16)
+    p = np.zeros(17, np.float32)
+    p[:16] = 1.0
+    net.set_params(p)
+    x = np.zeros((len(rows), 16), np.float32)
+    for i, r in enumerate(rows):
+        x[i, :len(r)] = r
+    y = net.forward(x)[:, 0].astype(np.float64)
+    assert list(y) == want_rz
+    # round to nearest would differ in every row
+    assert all(float(np.float32(sum(r))) != w for r, w in zip(rows, want_rz))
+    net.close()
+    # across k slabs: the 1 in slab 0, the small part in slab 1
+    net2 = kd.MLP([80, 1])
+    net2.set_precision(kd.KD_MLP_BF16)
+    p2 = np.zeros(81, np.float32)
+    p2[:80] = 1.0
+    net2.set_params(p2)
+    x2 = np.zeros((2, 80), np.float32)
+    x2[0, 0], x2[0, 70] = 1.0, 0.75 * u
+    x2[1, 0], x2[1, 70] = -1.0, -0.75 * u
+    assert list(net2.forward(x2)[:, 0].astype(np.float64)) == [1.0, -1.0]
+    net2.close()
