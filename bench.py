@@ -55,6 +55,10 @@ def parse():
     p.add_argument("--no-tc", action="store_true", help="skip the tensor-core precision form")
     p.add_argument("--no-hbm", action="store_true", help="skip the HBM-resident 4096x2048 grid")
     p.add_argument("--no-dw", action="store_true", help="skip the double-word (FP64-accurate) form")
+    p.add_argument("--profile-persist", default=None, metavar="N,CHUNK",
+                   help="run the persistent batch kernel on N runs for a profiler")
+    p.add_argument("--profile-mlp", default=None, metavar="BATCH,STEPS",
+                   help="run the BF16 tensor-core surrogate training for a profiler")
     p.add_argument("--profile-sweep", default=None, metavar="PREC,KIND,REPS[,GRID]",
                    help="profiling mode: build the GRID workload (1024x512 default, or 4096x2048), "
                         "step it twice, then run REPS back-to-back sweeps of KIND (0 x, 1 y) at "
@@ -438,6 +442,49 @@ def profile_sweep(spec: str):
     print("ok", prec, kind, reps, grid)
 
 
+def profile_persist(spec: str):
+    """The persistent batch kernel for a profiler: the first N runs of the 64-run batch
+    (FP32, launch variants fixed at the radix-4 pair (2, 2) that the tuner picks for these
+    grids), advanced in the persistent form by two calls of CHUNK steps, one launch of
+    k_persist each (ncu -k regex:k_persist -s 1 -c 1 captures the second)."""
+    from paper_2307_01571_gb300 import kd
+    n, chunk = (int(v) for v in spec.split(","))
+    members = W.c4()[:n]
+    sims = [kd.Sim.from_workload(w) for w in members]
+    for s_, w in zip(sims, members):
+        s_.sweep_variants = (2, 2)
+        s_.init_packet(w.packet)
+    with kd.Batch(sims) as b:
+        b.set_mode(kd.KD_BATCH_PERSISTENT)
+        for _ in range(2):
+            b.step([w.dt for w in members], chunk, obs_every=chunk)
+    for s_ in sims:
+        s_.get_time()
+        s_.close()
+    print("ok persistent", n, chunk)
+
+
+def profile_mlp(spec: str):
+    """The surrogate network's BF16 tensor-core GEMMs for a profiler: STEPS training steps
+    of the 5 -> 3 x 256 -> 4 network on BATCH seeded rows (each step: 4 forward, 7 backward
+    GEMMs of k_gemm_bf16)."""
+    import torch
+    from paper_2307_01571_gb300 import kd, surrogate as S
+    batch, steps = (int(v) for v in spec.split(","))
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(rng.standard_normal((batch, S.WIDTHS[0])).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((batch, S.WIDTHS[-1])).astype(np.float32)).cuda()
+    net = kd.MLP(S.WIDTHS)
+    net.set_precision(kd.KD_MLP_BF16)
+    net.set_params(S.he_init(S.WIDTHS, 0))
+    for _ in range(steps):
+        net.train_step(x.data_ptr(), t.data_ptr(), batch, 1e-3)
+    torch.cuda.synchronize()
+    net.get_params()
+    net.close()
+    print("ok mlp", batch, steps)
+
+
 def hbm_resident(kd, stream, hbm_peak, hbm_src, flush, tuned):
     """FP32 step on a grid whose state does not fit in L2 (4096x2048, 256 MiB spinor plus
     a 64 MiB kinetic table): 200 Strang steps with observations every 100, and each sweep
@@ -486,6 +533,10 @@ def main():
     args = parse()
     if args.profile_sweep:
         return profile_sweep(args.profile_sweep)
+    if args.profile_persist:
+        return profile_persist(args.profile_persist)
+    if args.profile_mlp:
+        return profile_mlp(args.profile_mlp)
     if args.impl == "reference":
         return run_reference(args)
     import torch

@@ -42,13 +42,17 @@ template <int LOGN, int AXIS, int VAR> struct Geo {
 };
 
 // one item of one sweep instantiation; not inlined, so that register allocation is per
-// instantiation (one function holding every path would spill)
+// instantiation (one function holding every path would spill).  Where K > 1 standalone
+// blocks share the CTA, each synchronises on its own named barrier (1 + part; 0 is the
+// CTA's, used between items), so the blocks do not wait for each other.
 template <int LOGN, int AXIS, int SHAPE, int VAR>
 __device__ __noinline__ void run_group(const SweepArgs& a, int g, unsigned char* smem, int nl) {
     using G = Geo<LOGN, AXIS, VAR>;
     using S = Sweep<float, LOGN, AXIS, SHAPE, G::V>;
+    static_assert(G::K <= 15, "named barriers 1 .. 15");
     const int part = threadIdx.x / G::TH;
-    S::template run_block<false>(a, g * G::K + part, threadIdx.x % G::TH, smem + part * G::Cf::SMEM_BYTES, nl);
+    S::template run_block<false>(a, g * G::K + part, threadIdx.x % G::TH, smem + part * G::Cf::SMEM_BYTES, nl,
+                                 G::K > 1 ? 1 + part : 0);
 }
 
 template <int AXIS, int SHAPE, int VAR>

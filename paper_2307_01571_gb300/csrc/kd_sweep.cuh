@@ -313,9 +313,19 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
     struct Ctx {
         int jt, bb, line, pair;
         int n_local;   // step of the current kd_step call the potential factor is taken at
+        int bar;       // barrier of the block's threads: 0 = the CTA's (see block_sync)
         bool valid;
         U* sm;
     };
+
+    // barrier of the THREADS threads that run one launch block: the CTA's own barrier in
+    // a standalone launch (bar 0, known at compile time there); a named barrier per block
+    // where several blocks share a CTA (the persistent batch kernel), so that they do not
+    // wait for each other
+    KD_DI static void block_sync(const Ctx& c) {
+        if (c.bar == 0) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(c.bar), "n"(Cf::THREADS) : "memory");
+    }
 
     KD_DI static int point_of(const SweepArgs& a, int line, int idx) {
         return AXIS == AXIS_X ? line * a.nx + idx : idx * a.nx + line;
@@ -439,7 +449,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
 #pragma unroll
                 for (int p = 0; p < NPL; ++p) sm[(wb ^ k) + p * PSTRIDE] = Unit<T>::pack(v + (m * R + r) * NC + p * CPP);
             }
-        __syncthreads();
+        block_sync(c);
 #pragma unroll
         for (int m = 0; m < E / RN; ++m)
 #pragma unroll
@@ -448,7 +458,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
 #pragma unroll
                 for (int p = 0; p < NPL; ++p) Unit<T>::unpack(sm[(rb ^ k) + p * PSTRIDE], v + (m * RN + r) * NC + p * CPP);
             }
-        if constexpr (!Cf::DB) __syncthreads();
+        if constexpr (!Cf::DB) block_sync(c);
     }
 
     // FFT with stages in plan order (REV = false) or reversed plan order (REV = true)
@@ -570,7 +580,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
                         fsh[2 * x + 1] = make_float4(f.sax.h, f.sax.l, 0.0f, 0.0f);
                     }
                 }
-            __syncthreads();
+            block_sync(c);
 #pragma unroll
             for (int m = 0; m < E / R; ++m)
 #pragma unroll
@@ -580,7 +590,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
                     const float4 f1 = c.valid ? fsh[2 * x + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
                     apply_potential_dw(c, v + (m * R + r) * NC, DW{f0.x, f0.y}, DW{f0.z, f0.w}, DW{f1.x, f1.y});
                 }
-            if constexpr (!Cf::DB) __syncthreads();
+            if constexpr (!Cf::DB) block_sync(c);
         }
     }
 
@@ -667,7 +677,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
                 }
             }
         if constexpr (Cf::SHARE) {
-            __syncthreads();
+            block_sync(c);
 #pragma unroll
             for (int m = 0; m < E / R; ++m)
 #pragma unroll
@@ -677,7 +687,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
                     apply_potential(c, v + (m * R + r) * NC, f.x, f.y, f.z);
                 }
             // single buffer: the next exchange writes over the factors
-            if constexpr (!Cf::DB) __syncthreads();
+            if constexpr (!Cf::DB) block_sync(c);
         }
     }
 
@@ -813,7 +823,7 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
 
     KD_DI static void run(const SweepArgs& a) {
         extern __shared__ __align__(16) unsigned char smem_raw[];
-        run_block<true>(a, (int)blockIdx.x, (int)threadIdx.x, smem_raw, a.n_local);
+        run_block<true>(a, (int)blockIdx.x, (int)threadIdx.x, smem_raw, a.n_local, 0);
     }
 
     // One launch block `blk` of the sweep, executed by the THREADS threads tid = 0..THREADS-1
@@ -822,9 +832,10 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
     // items after its own dependency wait (every thread of the CTA reaches the same
     // barriers: items of one kind run side by side with the same instantiation).
     template <bool PDL>
-    KD_DI static void run_block(const SweepArgs& a, int blk, int tid, unsigned char* smem, int n_local) {
+    KD_DI static void run_block(const SweepArgs& a, int blk, int tid, unsigned char* smem, int n_local, int bar) {
         Ctx c;
         c.n_local = n_local;
+        c.bar = bar;
         if (AXIS == AXIS_X) { c.bb = tid / TF; c.jt = tid % TF; }
         else { c.bb = tid % BATCH; c.jt = tid / BATCH; }
         // the pair index varies fastest so both pairs of a line tile run together; with
