@@ -6,7 +6,7 @@ population of the incoming peak, of the two-photon Bragg peak, and the spin-reso
 Bragg populations (same spin and flipped spin, Sec. III.B).  Training data come from the
 batched solver (``kd.Batch``), training and inference run in the library's own MLP
 kernels (``kd.MLP``); the solver stays the fallback outside the trained parameter box and
-the judge of the surrogate's error.
+the reference for the surrogate's error.
 
 Targets are log10 of the four populations (they span many decades); inputs and targets
 are standardised with the training set's mean and spread.
