@@ -107,23 +107,27 @@ __global__ void __launch_bounds__(256) k_gemm(const float* A, long sam, long sak
 // ------------------------------------------------------ BF16 tensor-core GEMM -----
 // The same product and epilogues as k_gemm with BF16 operands (rounded to nearest from
 // the FP32 inputs while staging) on the 5th-generation tensor cores, FP32 accumulation in
-// tensor memory.  One CTA of 128 threads computes a 128 x 64 tile of C: thread r owns row
-// m0 + r, which is TMEM lane r.  Per 64-deep k slab the threads stage A (128 x 64) and B
-// (64 x 64, n by k) in shared memory in the no-swizzle K-major canonical layout (8-row x
-// 16-byte core matrices: LBO = 128 B between core matrices along k, SBO = 1024 B between
-// 8-row groups), thread 0 issues four tcgen05.mma.kind::f16 (M 128, N 64, K 16; A and B
-// both BF16) and commits them to an mbarrier; all threads wait for it (bounded) before the
-// next slab overwrites the operands.  A wait that runs out sets *status and the CTA skips
-// the rest (the host reports KD_ERR_TIMEOUT).
+// tensor memory.  One CTA of 128 threads computes a 128 x 32 tile of C (narrow tiles: the
+// network's products are small, so more CTAs share them): thread r owns row m0 + r, which
+// is TMEM lane r.  The k dimension runs in 64-deep slabs through two shared-memory stages
+// in the no-swizzle K-major canonical layout (8-row x 16-byte core matrices: LBO = 128 B
+// between core matrices along k, SBO = 1024 B between 8-row groups): while thread 0's four
+// tcgen05.mma.kind::f16 (M 128, N 32, K 16; A and B both BF16) of slab j run, committed to
+// the stage's mbarrier, the threads load slab j + 1 from global memory (16-byte loads where
+// the operand is contiguous in k and aligned), wait for slab j - 1's products (bounded) and
+// store into the stage those freed.  A wait that runs out sets *status, the CTA issues no
+// further products, waits (bounded) for those in flight and skips the epilogue; the host
+// reports KD_ERR_TIMEOUT.
 namespace tcg {
+constexpr int BN = 32;                                   // columns of C per CTA
 constexpr uint32_t LBO = 128, SBO = 1024;
-constexpr uint32_t A_BYTES = 16 * SBO, B_BYTES = 8 * SBO;
-constexpr uint32_t OFF_A = 0, OFF_B = A_BYTES, OFF_BAR = A_BYTES + B_BYTES, OFF_SLOT = OFF_BAR + 8;
-constexpr uint32_t SMEM = OFF_SLOT + 8;
-constexpr uint32_t TMEM_COLS = 64;
+constexpr uint32_t A_BYTES = 16 * SBO, B_BYTES = (BN / 8) * SBO, STAGE = A_BYTES + B_BYTES;
+constexpr uint32_t OFF_BAR = 2 * STAGE, OFF_SLOT = OFF_BAR + 16;
+constexpr uint32_t SMEM = OFF_SLOT + 16;
+constexpr uint32_t TMEM_COLS = 32;
 // instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1), B BF16
 // (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
 constexpr long long WAIT_LIMIT = 1ll << 20;
 
@@ -146,92 +150,151 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     }
     return false;
 }
+// eight consecutive k of one operand row (element (row, k) at p[row * sr + k * sk]), zero
+// outside [0, K) or for rows out of range
+__device__ __forceinline__ void load8(const float* p, long sr, long sk, int row, bool row_ok, int k, int K,
+                                      float* v) {
+    const float* q = p + (long)row * sr + (long)k * sk;
+    if (row_ok && sk == 1 && k + 8 <= K && ((reinterpret_cast<uintptr_t>(q) & 15) == 0)) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(q));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(q) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (row_ok && k + e < K) ? __ldg(q + (long)e * sk) : 0.0f;
+    }
+}
 }  // namespace tcg
+
+// one 64-deep slab of A (128 rows: 8 chunks of 8 k per thread) and B (32 rows n: thread t
+// holds row t & 31, chunks 2 (t >> 5) and 2 (t >> 5) + 1) in registers
+struct Slab {
+    float a[8][8];
+    float b[2][8];
+};
+
+__device__ __forceinline__ void slab_load(const float* A, long sam, long sak, const float* B, long sbk, long sbn,
+                                          int m, int M, int n0, int N, int K, int k0, Slab& s) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) tcg::load8(A, sam, sak, m, m < M, k0 + 8 * c, K, s.a[c]);
+    const int nn = t & 31, n = n0 + nn;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) tcg::load8(B, sbn, sbk, n, n < N, k0 + 8 * (2 * (t >> 5) + h), K, s.b[h]);
+}
+
+__device__ __forceinline__ void slab_store(unsigned char* stage, const Slab& s) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t o = (uint32_t)(t >> 3) * tcg::SBO + (uint32_t)c * tcg::LBO + (uint32_t)(t & 7) * 16;
+        *reinterpret_cast<uint4*>(stage + o) =
+            make_uint4(tcg::pack_bf16(s.a[c][0], s.a[c][1]), tcg::pack_bf16(s.a[c][2], s.a[c][3]),
+                       tcg::pack_bf16(s.a[c][4], s.a[c][5]), tcg::pack_bf16(s.a[c][6], s.a[c][7]));
+    }
+    const int nn = t & 31;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = 2 * (t >> 5) + h;
+        const uint32_t o = (uint32_t)(nn >> 3) * tcg::SBO + (uint32_t)c * tcg::LBO + (uint32_t)(nn & 7) * 16;
+        *reinterpret_cast<uint4*>(stage + tcg::A_BYTES + o) =
+            make_uint4(tcg::pack_bf16(s.b[h][0], s.b[h][1]), tcg::pack_bf16(s.b[h][2], s.b[h][3]),
+                       tcg::pack_bf16(s.b[h][4], s.b[h][5]), tcg::pack_bf16(s.b[h][6], s.b[h][7]));
+    }
+}
 
 __global__ void __launch_bounds__(128) k_gemm_bf16(const float* A, long sam, long sak, const float* B,
                                                    long sbk, long sbn, float* C, float* Y, const float* bias,
                                                    int M, int N, int K, int epi, int* status) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int t = threadIdx.x, w = t >> 5;
-    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 64;
-    const uint32_t s0 = tcg::su32(sm), bar = s0 + tcg::OFF_BAR;
+    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * tcg::BN;
+    const uint32_t s0 = tcg::su32(sm);
+    const uint32_t bar[2] = {s0 + tcg::OFF_BAR, s0 + tcg::OFF_BAR + 8};
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(s0 + tcg::OFF_SLOT), "r"(tcg::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar[0]));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar[1]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *reinterpret_cast<const uint32_t*>(sm + tcg::OFF_SLOT);
-    uint32_t phase = 0;
-    bool ok = true;
     const int m = m0 + t;
-    for (int k0 = 0; k0 < K && ok; k0 += 64) {
-        // A row m (= TMEM lane t): 8 core chunks of 8 k
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            float v[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int k = k0 + 8 * c + e;
-                v[e] = (m < M && k < K) ? A[m * sam + k * sak] : 0.0f;
-            }
-            const uint32_t o = (uint32_t)(t >> 3) * tcg::SBO + (uint32_t)c * tcg::LBO + (uint32_t)(t & 7) * 16;
-            *reinterpret_cast<uint4*>(sm + tcg::OFF_A + o) =
-                make_uint4(tcg::pack_bf16(v[0], v[1]), tcg::pack_bf16(v[2], v[3]), tcg::pack_bf16(v[4], v[5]),
-                           tcg::pack_bf16(v[6], v[7]));
-        }
-        // B row n (= output column n0 + nn), k half hh: 4 core chunks of 8 k
-        {
-            const int nn = t & 63, hh = t >> 6, n = n0 + nn;
-#pragma unroll
-            for (int c4 = 0; c4 < 4; ++c4) {
-                const int c = 4 * hh + c4;
-                float v[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int k = k0 + 8 * c + e;
-                    v[e] = (n < N && k < K) ? B[k * sbk + n * sbn] : 0.0f;
-                }
-                const uint32_t o = (uint32_t)(nn >> 3) * tcg::SBO + (uint32_t)c * tcg::LBO + (uint32_t)(nn & 7) * 16;
-                *reinterpret_cast<uint4*>(sm + tcg::OFF_B + o) =
-                    make_uint4(tcg::pack_bf16(v[0], v[1]), tcg::pack_bf16(v[2], v[3]), tcg::pack_bf16(v[4], v[5]),
-                               tcg::pack_bf16(v[6], v[7]));
-            }
-        }
+    const int nslab = (K + 63) / 64;
+    uint32_t phase[2] = {0u, 0u};
+    bool ok = true;
+    int issued = 0;          // slabs whose products were issued (and committed)
+    int waited = 0;          // slabs whose products were waited for
+    Slab sl;
+    if (nslab > 0) {
+        slab_load(A, sam, sak, B, sbk, sbn, m, M, n0, N, K, 0, sl);
+        slab_store(sm, sl);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    for (int j = 0; j < nslab && ok; ++j) {
+        const int b = j & 1;
         if (t == 0) {
+            const uint32_t sa = s0 + (uint32_t)b * tcg::STAGE;
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t da = tcg::sdesc(s0 + tcg::OFF_A + (uint32_t)ks * 2 * tcg::LBO, tcg::LBO, tcg::SBO);
-                const uint64_t db = tcg::sdesc(s0 + tcg::OFF_B + (uint32_t)ks * 2 * tcg::LBO, tcg::LBO, tcg::SBO);
-                const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+                const uint64_t da = tcg::sdesc(sa + (uint32_t)ks * 2 * tcg::LBO, tcg::LBO, tcg::SBO);
+                const uint64_t db = tcg::sdesc(sa + tcg::A_BYTES + (uint32_t)ks * 2 * tcg::LBO, tcg::LBO, tcg::SBO);
+                const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                              :: "r"(tmem), "l"(da), "l"(db), "r"(tcg::IDESC), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(bar) : "memory");
+                         :: "r"(bar[b]) : "memory");
         }
-        const bool got = tcg::mbar_wait(bar, phase);
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        issued = j + 1;
+        // the next slab's global loads run while these products do
+        if (j + 1 < nslab) slab_load(A, sam, sak, B, sbk, sbn, m, M, n0, N, K, 64 * (j + 1), sl);
+        bool got = true;
+        if (j >= 1) {   // slab j - 1's products read the stage slab j + 1 goes to
+            got = tcg::mbar_wait(bar[b ^ 1], phase[b ^ 1]);
+            if (got) {
+                phase[b ^ 1] ^= 1u;
+                waited = j;
+            }
+        }
+        if (got && j + 1 < nslab) {
+            slab_store(sm + (uint32_t)(b ^ 1) * tcg::STAGE, sl);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         ok = __syncthreads_and(got) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    if (ok && K > 0) {
-        // row m's 64 columns from TMEM lane t: four 16-column loads
+    // the last issued slab's products (and, after a failed wait, those still in flight:
+    // each wait bounded, the first that runs out ends them)
+    while (waited < issued) {
+        const int b = waited & 1;
+        if (!tcg::mbar_wait(bar[b], phase[b])) {
+            ok = false;
+            break;
+        }
+        phase[b] ^= 1u;
+        ++waited;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok) != 0;
+    if (ok && nslab > 0) {
+        // row m's 32 columns from TMEM lane t: two 16-column loads
         const uint32_t trow = tmem + ((uint32_t)((w & 3) * 32) << 16);
-        uint32_t r[64];
+        uint32_t r[32];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 2; ++j)
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
                          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                          : "=r"(r[16 * j + 0]), "=r"(r[16 * j + 1]), "=r"(r[16 * j + 2]), "=r"(r[16 * j + 3]),
@@ -242,24 +305,17 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const float* A, long sam, lon
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (m < M) {
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
+            for (int j = 0; j < tcg::BN; ++j) {
                 const int n = n0 + j;
                 if (n >= N) break;
                 float c = __uint_as_float(r[j]);
                 if (epi >= 1) c += bias[n];
-                if (epi == 2) {
-                    C[(long)m * N + n] = c;
-                    Y[(long)m * N + n] = gelu(c);
-                } else {
-                    C[(long)m * N + n] = c;
-                }
+                C[(long)m * N + n] = c;
+                if (epi == 2) Y[(long)m * N + n] = gelu(c);
             }
         }
     }
-    if (!ok && t == 0) {
-        atomicOr(status, 1);
-        tcg::mbar_wait(bar, phase ^ 1u);   // products possibly in flight: bounded wait
-    }
+    if (!ok && t == 0) atomicOr(status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -330,16 +386,16 @@ __global__ void k_adam(float* p, const float* g, float* m1, float* m2, long n, f
 cudaError_t gemm(const kd_mlp* net, const float* A, long sam, long sak, const float* B, long sbk, long sbn,
                  float* C, float* Y, const float* bias, int M, int N, int K, int epi, cudaStream_t s) {
     if (net->prec == KD_MLP_BF16) {
-        // at least 28 KB of shared memory per CTA: at most 8 CTAs per SM, so their tensor
-        // memory (64 columns each) fits the SM's 512 columns without waiting
+        // two 20 KB stages: at most 5 CTAs per SM, whose tensor memory (32 columns each)
+        // fits the SM's 512 columns, so no allocation waits
         static bool attr = false;
-        constexpr int smem = tcg::SMEM > 28 * 1024 ? (int)tcg::SMEM : 28 * 1024;
+        constexpr int smem = (int)tcg::SMEM;
         if (!attr) {
             cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        dim3 grid((N + 63) / 64, (M + 127) / 128);
+        dim3 grid((N + tcg::BN - 1) / tcg::BN, (M + 127) / 128);
         k_gemm_bf16<<<grid, 128, smem, s>>>(A, sam, sak, B, sbk, sbn, C, Y, bias, M, N, K, epi, net->status);
         return cudaGetLastError();
     }
