@@ -177,6 +177,34 @@ def test_persistent_batch_against_oracle(kd):
         s.close()
 
 
+def test_persistent_batch_many_members_equals_graph_form(kd):
+    """150 small members (three grid shapes, seeded fields): far more members than the
+    kernel keeps in registers or shared memory, so every item's member lookup runs over the
+    prefix sums; the persistent form equals the graph-branch form bit for bit (both on the
+    variants the kernel holds), over two calls with observations."""
+    rng = np.random.default_rng(11)
+    shapes = [(16, 16), (32, 16), (16, 64)]
+    wls = [W.small(*shapes[i % 3], W.GAUSS, units=W.ATOMIC, a0=float(rng.uniform(0.05, 0.4)))
+           for i in range(150)]
+    finals = {}
+    for mode in (kd.KD_BATCH_GRAPH, kd.KD_BATCH_PERSISTENT):
+        sims = [kd.Sim.from_workload(wl.with_(precision=1)) for wl in wls]
+        for s, wl in zip(sims, wls):
+            s.sweep_variants = PERSIST_VARIANTS
+            s.init_packet(wl.packet)
+        with kd.Batch(sims) as b:
+            b.set_mode(mode)
+            o1 = b.step([wl.dt for wl in wls], 12, obs_every=6)
+            o2 = b.step([wl.dt for wl in wls], 7, obs_every=6)
+        finals[mode] = ([s.get_spinor() for s in sims], [a + c for a, c in zip(o1, o2)])
+        for s in sims:
+            s.close()
+    (pg, og), (pp, op) = finals[kd.KD_BATCH_GRAPH], finals[kd.KD_BATCH_PERSISTENT]
+    for i in range(len(wls)):
+        assert np.array_equal(pg[i], pp[i]), i
+        assert og[i] == op[i], i
+
+
 def test_persistent_batch_withheld_producer_times_out(kd):
     """A member's first work item never signals completion (test hook): the items waiting
     for it give up after their bounded waits, the call returns KD_ERR_TIMEOUT, and the
