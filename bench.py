@@ -105,6 +105,41 @@ def ncu_traffic(kernel: str, form: str):
         return None
 
 
+def ncu_instructions(kernel: str, form: str):
+    """Warp instructions per launch from the committed ncu summary (smsp__inst_executed.sum),
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            e = json.load(fh)[f"{kernel}_{form}"]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return e.get("warp_instructions_per_launch")
+    except Exception:
+        return None
+
+
+def roofline_issue(form: str, sweep_ms: dict, sm_mhz, sms: int, profiled_variants: bool = True) -> dict:
+    """The sweeps against their instruction-issue bound: warp instructions per launch (ncu)
+    over the launch time, against one warp instruction per clock per scheduler (four per
+    SM) at the SM clock sampled during the timed region.  The bound says how close a
+    kernel is to what its instruction count allows, whatever memory it moves."""
+    peak = 4.0 * sms * (sm_mhz or 0.0) * 1e6
+    out = {"bound": "issue", "unit": "warp instructions/s", "peak": peak,
+           "peak_source": f"4 schedulers x {sms} SMs x {sm_mhz} MHz (sampled)", "kernels": {}}
+    for kern, ms in sweep_ms.items():
+        # the counts were taken on the default launch variants (bench.py --profile-sweep)
+        inst = ncu_instructions(kern, form) if profiled_variants else None
+        if inst is None or not peak:
+            out["kernels"][kern] = {"warp_instructions_per_launch": None, "frac": None}
+            continue
+        ach = inst / (ms * 1e-3)
+        out["kernels"][kern] = {"warp_instructions_per_launch": inst, "achieved": ach,
+                                "frac": ach / peak, "launch_ms": round(ms, 5),
+                                "time_at_full_issue_us": inst / peak * 1e6}
+    return out
+
+
 class Clocks:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -688,6 +723,9 @@ def main():
         "clocks": clk,
         "norm_drift_fp32": drift,
     }
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    line["roofline_issue"] = roofline_issue("fp32", sweep_ms, (clk or {}).get("sm_mhz"), sms,
+                                            tuple(tune["variants"]) == (0, 0))
     e2e_v, bi, bo = e2e_form(W.FP32, K)
     line["e2e"] = {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": bi,
                    "d2h_bytes_per_step": bo}
@@ -706,7 +744,8 @@ def main():
         line["dw"] = {"value": vd, "unit": UNIT, "ms_per_step": msd / Kd, "steps": Kd,
                       "dtype": "f32 pairs (double-word, 48-bit significand)",
                       "norm_drift": driftd, "gpu_launches": ld,
-                      "roofline_hbm": roofline("dw", wld, swd, hbm)}
+                      "roofline_hbm": roofline("dw", wld, swd, hbm),
+                      "roofline_issue": roofline_issue("dw", swd, (line.get("clocks") or {}).get("sm_mhz"), sms)}
         if "fp64" in line:
             line["dw"]["speedup_over_fp64"] = vd / line["fp64"]["value"]
     if rank == 0 and not args.no_tc:
