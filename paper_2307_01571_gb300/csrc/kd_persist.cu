@@ -109,7 +109,8 @@ __device__ __forceinline__ int find_member(const int* pre, int n, int r) {
 
 __global__ void __launch_bounds__(kThreads, 3) k_persist(const PersistPlan p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item, s_go;
+    // the current item, decoded by warp 0 (read by every thread after the item's barrier)
+    __shared__ int s_go, s_item, s_m, s_g, s_i, s_ysweep, s_closing;
     // the item's sweep arguments, staged in shared memory (read many times by every thread)
     __shared__ __align__(16) SweepArgs s_args;
     const PersistMember* mem = p.members;
@@ -119,53 +120,70 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const PersistPlan p) {
     int next_item = 0;
     if (threadIdx.x == 0) next_item = (int)atomicAdd(p.next, 1u);
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_item = next_item;
-            s_go = next_item < total && *(volatile const int*)p.abort == 0;
-            if (s_go) next_item = (int)atomicAdd(p.next, 1u);
-        }
-        __syncthreads();
-        const int item = s_item;
-        if (!s_go) break;
-        const int i = item / S;                 // step of the chunk, 0-based
-        int r = item % S;
-        const bool ysweep = r < p.y_items;
-        if (!ysweep) r -= p.y_items;
-        const int m = find_member(ysweep ? p.pre_y : p.pre_x, p.n, r);
-        const PersistMember& M = mem[m];
-        const int g = r - (ysweep ? p.pre_y[m] : p.pre_x[m]);
-        // dependency: every item of member m before this sweep
-        const unsigned need = (unsigned)(i * (M.iy + M.ix) + (ysweep ? 0 : M.iy));
-        if (threadIdx.x == 0) {
-            int go = 1;
-            if (ld_acquire(p.done + m) < need) {
-                const long long t0 = clock64();
-                while (ld_acquire(p.done + m) < need) {
-                    if (*(volatile const int*)p.abort) { go = 0; break; }
-                    if (clock64() - t0 > p.budget_cycles) {
-                        atomicExch(p.abort, 1);
-                        atomicOr(M.status, KD_STATUS_TC_TIMEOUT);
-                        go = 0;
-                        break;
+        if (threadIdx.x < 32) {
+            // warp 0: lane 0 takes the item, decodes it and waits for its dependency; the
+            // warp stages its arguments; one CTA barrier then publishes all of it
+            int go = 0, item = 0, m = 0, g = 0, i = 0, ysweep = 0, closing = 0;
+            if (threadIdx.x == 0) {
+                item = next_item;
+                go = item < total && *(volatile const int*)p.abort == 0;
+                if (go) {
+                    next_item = (int)atomicAdd(p.next, 1u);
+                    i = item / S;            // step of the chunk, 0-based
+                    int r = item % S;
+                    ysweep = r < p.y_items;
+                    if (!ysweep) r -= p.y_items;
+                    const int* pre = ysweep ? p.pre_y : p.pre_x;
+                    m = find_member(pre, p.n, r);
+                    g = r - pre[m];
+                    closing = !ysweep && i + 1 == p.chunk && p.closing;
+                    // dependency: every item of member m before this sweep
+                    const PersistMember& M = mem[m];
+                    const unsigned need = (unsigned)(i * (M.iy + M.ix) + (ysweep ? 0 : M.iy));
+                    if (ld_acquire(p.done + m) < need) {
+                        const long long t0 = clock64();
+                        while (ld_acquire(p.done + m) < need) {
+                            if (*(volatile const int*)p.abort) { go = 0; break; }
+                            if (clock64() - t0 > p.budget_cycles) {
+                                atomicExch(p.abort, 1);
+                                atomicOr(M.status, KD_STATUS_TC_TIMEOUT);
+                                go = 0;
+                                break;
+                            }
+                            __nanosleep(128);
+                        }
                     }
-                    __nanosleep(128);
                 }
             }
-            s_go = go;
+            const unsigned full = 0xffffffffu;
+            go = __shfl_sync(full, go, 0);
+            m = __shfl_sync(full, m, 0);
+            ysweep = __shfl_sync(full, ysweep, 0);
+            closing = __shfl_sync(full, closing, 0);
+            if (go) {
+                const PersistMember& M = mem[m];
+                const int4* src = reinterpret_cast<const int4*>(ysweep ? &M.y : (closing ? &M.xc : &M.x));
+                int4* dst = reinterpret_cast<int4*>(&s_args);
+                for (int w = threadIdx.x; w < (int)(sizeof(SweepArgs) / sizeof(int4)); w += 32) dst[w] = src[w];
+            }
+            if (threadIdx.x == 0) {
+                s_go = go;
+                s_item = item;
+                s_m = m;
+                s_g = g;
+                s_i = i;
+                s_ysweep = ysweep;
+                s_closing = closing;
+            }
         }
         __syncthreads();
         if (!s_go) break;
-        const bool closing = !ysweep && i + 1 == p.chunk && p.closing;
-        {
-            const int4* src = reinterpret_cast<const int4*>(ysweep ? &M.y : (closing ? &M.xc : &M.x));
-            int4* dst = reinterpret_cast<int4*>(&s_args);
-            for (int w = threadIdx.x; w < (int)(sizeof(SweepArgs) / sizeof(int4)); w += kThreads) dst[w] = src[w];
-        }
-        __syncthreads();
+        const int m = s_m, i = s_i, ysweep = s_ysweep, closing = s_closing;
+        const PersistMember& M = mem[m];
         // the item's CTA-fulls of blocks, one after the other (a barrier between them, so
         // that no thread writes shared memory another still reads)
         const int per = ysweep ? M.gy : M.gx, nct = ysweep ? M.cy : M.cx;
-        const int c0 = g * per, c1 = c0 + per < nct ? c0 + per : nct;
+        const int c0 = s_g * per, c1 = c0 + per < nct ? c0 + per : nct;
         for (int cf = c0; cf < c1; ++cf) {
             if (cf > c0) __syncthreads();
             if (ysweep) run_logn<AXIS_Y, SHAPE_F1F2>(M.ly, M.vy_alt, s_args, cf, smem, 0);
@@ -173,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const PersistPlan p) {
             else run_logn<AXIS_X, SHAPE_F1F2>(M.lx, M.vx_alt, s_args, cf, smem, i + 1);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && item != p.hold_item) {
+        if (threadIdx.x == 0 && s_item != p.hold_item) {
             // release at GPU scope: the CTA's stores (ordered before this thread by the
             // barrier) are visible to whoever acquires the new count
             asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p.done + m), "r"(1u) : "memory");
