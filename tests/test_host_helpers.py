@@ -47,3 +47,21 @@ def test_surrogate_error_report_and_worst_cases():
     w = surrogate.worst_cases(pred, truth, params, k=2)
     assert [c["params"]["w0_lambda"] for c in w["log10_P_in"]] == [15.0, 35.0]
     assert w["log10_P_in"][0]["pred"][0] == 1.5 and w["log10_P_in"][0]["truth"][0] == 0.0
+
+
+def test_issue_bound_reads_the_committed_counts_only_for_the_current_source():
+    import bench
+    counts = {k: bench.ncu_instructions(k, f) for k, f in (("x_sweep", "fp32"), ("y_sweep", "fp32"))}
+    r = bench.roofline_issue("fp32", {"x_sweep": 0.0131, "y_sweep": 0.0131}, 2070.0, 152)
+    assert abs(r["peak"] - 4 * 152 * 2070e6) < 1.0
+    for k, inst in counts.items():
+        got = r["kernels"][k]
+        if inst is None:   # counts taken on another kernel source: not reported
+            assert got["frac"] is None
+        else:
+            assert got["warp_instructions_per_launch"] == inst
+            assert abs(got["frac"] - inst / (0.0131e-3 * r["peak"])) < 1e-12
+            assert abs(got["time_at_full_issue_us"] - inst / r["peak"] * 1e6) < 1e-9
+    # launch variants other than the profiled ones: no count
+    r2 = bench.roofline_issue("fp32", {"x_sweep": 0.0131}, 2070.0, 152, profiled_variants=False)
+    assert r2["kernels"]["x_sweep"]["frac"] is None
