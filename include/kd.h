@@ -256,8 +256,9 @@ int kd_batch_set_mode(kd_batch* batch, int32_t mode);
 /* Surrogate network (a learned stand-in for the solver's read-outs; the paper has no network): a fully
  * connected MLP, widths[0] inputs -> ... -> widths[nlayers] outputs, exact-erf GELU on the
  * hidden layers, linear output, trained with mean squared error and Adam
- * (beta = 0.9, 0.999, eps = 1e-8) by hand-written FP32 kernels; every reduction runs in a
- * fixed order (bitwise reproducible).  Parameters are laid out per layer as W_l
+ * (beta = 0.9, 0.999, eps = 1e-8) by hand-written kernels (FP32; the matrix products
+ * optionally on BF16 tensor cores, kd_mlp_set_precision); every reduction runs in a fixed
+ * order (bitwise reproducible).  Parameters are laid out per layer as W_l
  * [widths[l+1]][widths[l]] row-major followed by b_l; the caller initialises them
  * (kd_mlp_set_params, which also resets Adam).  Row-major float batches [batch][width].
  * kd_mlp_train_step takes device pointers and is asynchronous on cuda_stream; loss_dev
