@@ -312,3 +312,34 @@ def test_largest_grids_free_plane_wave_is_exact(kd, prec, n):
     exp = (ph_y[rows, None, None] * ph_x[None, :, None]) * us[None, None, :] * ref_phase
     err = np.max(np.abs(got[rows] - exp))
     assert err <= (1e-10 if prec == 0 else 2e-4), err
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_degenerate_cases(kd, prec):
+    """Zero steps leave state and clock untouched; a Gaussian beam of zero amplitude
+    advances exactly like the free particle (its potential factor is the identity: cos 0 - 1
+    = 0 and sin 0 = 0, so the pointwise update adds exact zeros); a batch of one member
+    with zero steps is a no-op too.  Both against the oracle's free-particle step."""
+    tol = {0: 1e-10, 1: 1e-4, 3: 1e-10}[prec]
+    free = W.small(64, 32, W.NONE, units=W.ATOMIC, nsteps=5)
+    beam0 = W.small(64, 32, W.GAUSS, units=W.ATOMIC, a0=0.0, nsteps=5)
+    psi0 = W.random_spinor(64, 32, 5)
+    u, g = free.units, free.grid
+    ref = oracle.step(u, g, free.field, psi0, 0.0, free.dt, 5)
+    out = {}
+    for name, wl in (("free", free), ("beam0", beam0)):
+        with kd.Sim.from_workload(wl.with_(precision=prec)) as sim:
+            sim.set_spinor(psi0)
+            before = sim.get_spinor()
+            assert sim.step(wl.dt, 0) == []
+            assert np.array_equal(sim.get_spinor(), before)
+            assert sim.get_time()[1] == 0
+            with kd.Batch([sim]) as b:
+                b.step([wl.dt], 0)
+            assert np.array_equal(sim.get_spinor(), before)
+            sim.step(wl.dt, 5)
+            assert sim.get_time()[1] == 5
+            out[name] = sim.get_spinor()
+    assert np.array_equal(out["free"], out["beam0"])
+    got = out["free"].astype(np.complex128)
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
