@@ -31,7 +31,7 @@ def _free_bytes():
     return torch.cuda.mem_get_info()[0]
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 @pytest.mark.parametrize("obs_every", [0, 20])
 def test_cancel_before_step_runs_one_closed_chunk(kd, prec, obs_every):
     wl = W.small(64, 32, W.GAUSS, units=W.ATOMIC, a0=0.3, precision=prec)
@@ -74,7 +74,7 @@ def test_cancel_from_another_thread(kd):
         assert np.array_equal(ref.get_spinor(), got)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_alloc_failure_in_create_releases_everything(kd, prec):
     wl = W.small(1024, 64, W.GAUSS, units=W.ATOMIC, precision=prec)
     kd.Sim.from_workload(wl).close()          # kernels and runtime state loaded once
