@@ -75,6 +75,19 @@ KD_DWI DW dw_add(DW x, DW y) {
     return fast_two_sum(s.h, w);
 }
 KD_DWI DW dw_sub(DW x, DW y) { return dw_add(x, dw_neg(y)); }
+// Lazy sums for a butterfly's first level: x + y as (h, l) with h = fl(x.h + y.h) exact to
+// its TwoSum error and l = that error plus both low parts, not renormalised (|l| may exceed
+// half an ulp of h).  dw_add_lazy then adds two such pairs and renormalises once: the
+// result has the sloppy double-word sum's absolute error bound (a few 2^-48 of the summed
+// magnitudes) with one Fast2Sum instead of three.
+KD_DWI DW dw_add_part(DW x, DW y) {
+    const DW s = two_sum(x.h, y.h);
+    return DW{s.h, f_add(s.l, f_add(x.l, y.l))};
+}
+KD_DWI DW dw_add_lazy(DW x, DW y) {
+    const DW s = two_sum(x.h, y.h);
+    return fast_two_sum(s.h, f_add(s.l, f_add(x.l, y.l)));
+}
 // x + y with y a float
 KD_DWI DW dw_add_f(DW x, float y) {
     const DW s = two_sum(x.h, y);

@@ -65,6 +65,21 @@ template <int DIR, int S, typename C> KD_DI void dft4(C* a) {
     a[3 * S] = csub(d02, r);
 }
 
+// The same four-point DFT on double-word values: the first level's sums and differences
+// stay unnormalised (dw_add_part) and each output renormalises once (dw_add_lazy)
+template <int DIR, int S> KD_DI void dft4(DWC* a) {
+    const DW s02x = dw_add_part(a[0].x, a[2 * S].x), s02y = dw_add_part(a[0].y, a[2 * S].y);
+    const DW d02x = dw_add_part(a[0].x, dw_neg(a[2 * S].x)), d02y = dw_add_part(a[0].y, dw_neg(a[2 * S].y));
+    const DW s13x = dw_add_part(a[S].x, a[3 * S].x), s13y = dw_add_part(a[S].y, a[3 * S].y);
+    const DW d13x = dw_add_part(a[S].x, dw_neg(a[3 * S].x)), d13y = dw_add_part(a[S].y, dw_neg(a[3 * S].y));
+    // r = (DIR i) d13
+    const DW rx = DIR > 0 ? dw_neg(d13y) : d13y, ry = DIR > 0 ? d13x : dw_neg(d13x);
+    a[0] = DWC{dw_add_lazy(s02x, s13x), dw_add_lazy(s02y, s13y)};
+    a[2 * S] = DWC{dw_add_lazy(s02x, dw_neg(s13x)), dw_add_lazy(s02y, dw_neg(s13y))};
+    a[S] = DWC{dw_add_lazy(d02x, rx), dw_add_lazy(d02y, ry)};
+    a[3 * S] = DWC{dw_add_lazy(d02x, dw_neg(rx)), dw_add_lazy(d02y, dw_neg(ry))};
+}
+
 // multiply by 1/sqrt(2) as a hi + lo pair: a single rounded constant would make every
 // radix-8 butterfly shrink the norm of two of its eight inputs by 2 h^2 - 1 (about 4e-8
 // in FP32), a bias that accumulates over thousands of steps
