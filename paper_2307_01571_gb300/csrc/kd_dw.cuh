@@ -119,6 +119,22 @@ KD_DWI DW dw_dot2(DW a, DW x, DW b, DW y) {
     return fast_two_sum(s.h, t);
 }
 
+// The same dot product without the final renormalisation (|l| may exceed half an ulp of
+// h): for values that go straight into a butterfly's first level (dw_add_part / dw_add),
+// whose TwoSum of the high parts is exact whatever the low parts are
+KD_DWI DW dw_dot2_part(DW a, DW x, DW b, DW y) {
+    const DW p = two_prod(a.h, x.h);
+    const DW q = two_prod(b.h, y.h);
+    const DW s = two_sum(p.h, q.h);
+    float t = f_add(p.l, q.l);
+    t = f_add(t, s.l);
+    t = f_fma(a.h, x.l, t);
+    t = f_fma(a.l, x.h, t);
+    t = f_fma(b.h, y.l, t);
+    t = f_fma(b.l, y.h, t);
+    return DW{s.h, t};
+}
+
 // Splits a double into the nearest double-word (exact for the 48 leading bits); host or
 // device, FP64.
 KD_DWI DW dw_from_double(double d) {
@@ -223,6 +239,11 @@ KD_DWI DWC dwc_sub(DWC a, DWC b) { return DWC{dw_sub(a.x, b.x), dw_sub(a.y, b.y)
 // a * w, w = (c, s): (a.x c - a.y s, a.x s + a.y c)
 KD_DWI DWC dwc_mul(DWC a, DWC w) {
     return DWC{dw_dot2(a.x, w.x, dw_neg(a.y), w.y), dw_dot2(a.x, w.y, a.y, w.x)};
+}
+// a * w unnormalised (dw_dot2_part): the FFT's twiddle products, which feed the next
+// butterfly directly
+KD_DWI DWC dwc_mul_part(DWC a, DWC w) {
+    return DWC{dw_dot2_part(a.x, w.x, dw_neg(a.y), w.y), dw_dot2_part(a.x, w.y, a.y, w.x)};
 }
 // a * r for a real double-word r
 KD_DWI DWC dwc_mul_r(DWC a, DW r) { return DWC{dw_mul(a.x, r), dw_mul(a.y, r)}; }

@@ -418,11 +418,13 @@ template <typename T, int LOGN, int AXIS, int SHAPE, int V> struct Sweep {
                         }
                     } else if constexpr (DWF) {
                         // double-word twiddle (c_hi, s_hi, c_lo, s_lo), unit modulus far
-                        // below the double-word rounding unit
+                        // below the double-word rounding unit; the products stay
+                        // unnormalised into this stage's butterfly, whose first level adds
+                        // their high parts exactly and renormalises
                         const float4 w4 = __ldg(reinterpret_cast<const float4*>(a.tw) + idx);
                         const DWC w = DWC{DW{w4.x, w4.z}, DIR > 0 ? DW{-w4.y, -w4.w} : DW{w4.y, w4.w}};
 #pragma unroll
-                        for (int q = 0; q < NC; ++q) b[r * NC + q] = dwc_mul(b[r * NC + q], w);
+                        for (int q = 0; q < NC; ++q) b[r * NC + q] = dwc_mul_part(b[r * NC + q], w);
                     } else {
                         C w = __ldg(reinterpret_cast<const C*>(a.tw) + idx);
                         if (DIR > 0) w.y = -w.y;
